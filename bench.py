@@ -1,0 +1,297 @@
+"""Benchmark of the GB300 TV-L1 optical-flow library.
+
+Workload (default): one 640 x 480 pair -- gradient-noise texture under an affine motion (rotation
+2 deg, zoom 1.03, translation (3, -2)) plus a 120 x 80 box moving (6, 4), noise sigma 0.01 --
+solved with pADMM (c = 0.05, a = 8, beta = 0.05, lambda = 5) over 5 pyramid levels (scale 0.5),
+10 warps per level and 100 inner iterations per warp: 409.2 Mpix*iter per flow.  A step is one
+whole solve of that pair (every row of the hot path: pyramid, level transfer, derivatives,
+warping, inner iterations, residual/energy reductions).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun, one rank per GPU) every rank solves its own copy of the workload
+(independent pairs: weak scaling, no data-path collective); value = pairs of all ranks / max
+rank time.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "flows/s & Mpix·iter/s vs plain GPU at EPE≤1e-2px to FP64; p50/p99 latency"
+H, W = 480, 640
+LEVELS, WARPS, ITERS = 5, 10, 100
+LAM, BETA = 5.0, 0.05
+WORKLOAD = "640x480 affine+box pair, pADMM, 5 levels x 10 warps x 100 iters"
+
+
+def mpix_iter_per_flow(levels=LEVELS, warps=WARPS, iters=ITERS, h=H, w=W, eta=0.5, lo=0):
+    import math
+    hs, ws = [h], [w]
+    for _ in range(1, levels):
+        hs.append(max(1, int(math.floor(hs[-1] * eta + 0.5))))
+        ws.append(max(1, int(math.floor(ws[-1] * eta + 0.5))))
+    return sum(hs[l] * ws[l] for l in range(lo, levels)) * warps * iters / 1e6
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_oracle_rate(sample_levels=3):
+    """Times the FP64 oracle, as it stands, on a bounded sample of the workload: the coarsest
+    `sample_levels` levels of the same pyramid and schedule (the full schedule minus the two
+    finest levels).  Returns (Mpix*iter/s, seconds, sample description, result flow)."""
+    import oracle
+    from paper_2011_10979_gb300 import synth
+    pr = synth.affine_rect_pair()
+    lo = LEVELS - sample_levels
+    P = oracle.Params(method=0, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS, out_level=lo)
+    t = time.perf_counter()
+    u, v, _, _ = oracle.solve(pr.I0, pr.I1, P)
+    dt = time.perf_counter() - t
+    work = mpix_iter_per_flow(lo=lo)
+    # the pyramid of the two finest levels is built as well: count only the iteration work
+    desc = "levels %d..%d of the 640x480 schedule (%.1f Mpix*iter, %.1f s), single thread" % (lo, LEVELS - 1, work, dt)
+    return work / dt, dt, desc, (u, v)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    times = []
+    for k in range(args.warmup + args.steps):
+        rate, dt, desc, _ = cpu_oracle_rate()
+        if k >= args.warmup:
+            times.append(rate)
+    rate = float(np.mean(times))
+    value = rate / mpix_iter_per_flow()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "flows/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "mpix_iter_per_s": rate,
+            "cpu_baseline": {"value": value, "unit": "flows/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "flows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_2011_10979_gb300 import flow, synth
+    from paper_2011_10979_gb300.build import build
+    build()
+    ctx = flow.Context(dev.index)
+    pr = synth.affine_rect_pair(seed=1 + rank)
+    I0, I1 = torch.from_numpy(pr.I0).to(dev), torch.from_numpy(pr.I1).to(dev)
+    P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def step():
+        return flow.of_solve(ctx, I0, I1, P, stats=False)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    sampler.start()
+    for k in range(args.steps):
+        flush.zero_()                       # evict the previous step's data from L2
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = float(np.sum(ms)) / args.steps / 1e3
+    # end to end through the host entry point: pinned host images in, host flow out
+    h0 = torch.from_numpy(pr.I0).pin_memory()
+    h1 = torch.from_numpy(pr.I1).pin_memory()
+    hu = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    hv = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        flow.of_solve_host_ptrs(ctx, h0.data_ptr(), h1.data_ptr(), H, W, P, hu.data_ptr(), hv.data_ptr())
+    barrier()
+    t0 = time.perf_counter()
+    n_e2e = max(3, args.steps)
+    for _ in range(n_e2e):
+        flow.of_solve_host_ptrs(ctx, h0.data_ptr(), h1.data_ptr(), H, W, P, hu.data_ptr(), hv.data_ptr())
+    barrier()
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_step, t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step, t_e2e = float(t[0]), float(t[1])
+    # dominant kernel: the fused pADMM iteration at the finest level, timed alone with CUDA events
+    roof = kernel_roofline(flow, torch, dev, pr)
+    launches = flow.lib().of_solve_kernel_count(ctx.h, H, W, P)
+    # plain single-pair FP32 GPU path (one kernel per operator), same workload
+    Pp = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
+                             engine=flow.OF_ENGINE_PLAIN)
+    flow.of_solve(ctx, I0, I1, Pp, stats=False)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        flow.of_solve(ctx, I0, I1, Pp, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_plain = e0.elapsed_time(e1) / 3 / 1e3
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1:
+        rate, dt, desc, (ou, ov) = cpu_oracle_rate()
+        # accuracy of the timed path on the sampled levels
+        Ps = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
+                                 out_level=LEVELS - 3)
+        gu, gv, _, _ = flow.of_solve(ctx, I0, I1, Ps, stats=False)
+        gu, gv = gu.double().cpu().numpy(), gv.double().cpu().numpy()
+        epe = float(np.hypot(gu - ou, gv - ov).mean())
+        cpu = {"value": rate / mpix_iter_per_flow(), "unit": "flows/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "epe_vs_gpu_px": epe, "max_abs_du_px": float(np.max(np.abs(gu - ou)))}
+    work = mpix_iter_per_flow()
+    value = ws / t_step
+    line = {"metric": METRIC, "value": value, "unit": "flows/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H, "W": W, "levels": LEVELS, "warps": WARPS, "iters": ITERS,
+                       "method": "pADMM", "lambda": LAM, "beta": BETA, "storage": "fp32",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if ws > 1 else "single"},
+            "mpix_iter_per_s": work * ws / t_step,
+            "plain_gpu": {"value": 1.0 / t_plain, "unit": "flows/s", "engine": "plain (one kernel per operator)",
+                          "speedup": t_plain / t_step},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": ws / t_e2e, "unit": "flows/s", "h2d_bytes_per_step": 2 * H * W * 4,
+                    "d2h_bytes_per_step": 2 * H * W * 4},
+            "gpu_launches": int(launches) * args.steps,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def kernel_roofline(flow, torch, dev, pr, iters=200):
+    """Average duration of the fused pADMM iteration kernel on the 640 x 480 level (CUDA events
+    on its stream, 200 back-to-back launches through of_admm_iterate) and its algorithmic
+    traffic: 13 planes read + 10 written, FP32 = 92 B per pixel-iteration."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    rng = np.random.default_rng(0)
+    st = {k: torch.zeros((H, W), dtype=torch.float32, device=dev)
+          for k in ("w", "u", "v", "p1", "p2", "q11", "q12", "q21", "q22", "s")}
+    Ix = torch.from_numpy((rng.normal(size=(H, W)) * 0.05).astype(np.float32)).to(dev)
+    Iy = torch.from_numpy((rng.normal(size=(H, W)) * 0.05).astype(np.float32)).to(dev)
+    It = torch.from_numpy((rng.normal(size=(H, W)) * 0.02).astype(np.float32)).to(dev)
+    at = float((BETA ** 2 + Ix.double() ** 2 + Iy.double() ** 2).max())
+    P = flow.default_params(lam=LAM, beta=BETA)
+    stream = torch.cuda.current_stream(dev)
+    flow.of_admm_iterate(st, Ix, Iy, It, at, P, 10, want_res=False)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    flow.of_admm_iterate(st, Ix, Iy, It, at, P, iters, want_res=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / iters / 1e3
+    bytes_per_launch = 92.0 * H * W
+    achieved = bytes_per_launch / t / 1e9
+    return {"kernel": "k_admm_fused<float,true,0> (640x480 level)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
+            "traffic": None, "us_per_launch": t * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * tvl1flow.h -- C ABI of the GB300 TV-L1 optical-flow library.
+ *
+ * The library solves the illumination-invariant isotropic TV-L1 optical-flow model
+ *     min_{w,u,v} ||grad w||_1 + ||grad (u,v)||_1 + lambda ||Ix u + Iy v + beta w + It||_1
+ * (Sun, Tai & Yuan, "Variational Image Motion Estimation by Accelerated Dual Optimization",
+ * Sec. 1 eq. (l1:optical:flow) and Sec. 2.2 eq. (l1:finite)) with the paper's preconditioned
+ * dual solvers -- rpADMMI / pADMM and rpADMMII (Sec. 3.1.1), Zach-pADMM (beta = 0, Sec.
+ * 3.1.1) and pDR with red-black symmetric Gauss-Seidel preconditioning (Sec. 3.1.2) -- inside
+ * a coarse-to-fine pyramid with bilinear warping (Sec. 4).  All arithmetic runs in CUDA kernels
+ * for sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point:
+ *  - Images and fields are single-channel, row-major, H rows x W columns, with a row pitch
+ *    `pitch` given in ELEMENTS (pitch >= W).  x runs along columns, y along rows.
+ *  - Flow sign: I1(x + u, y + v) ~ I0(x, y); u is horizontal (+columns), v vertical (+rows).
+ *  - Unless a name ends in `_host`, every array pointer is a DEVICE pointer owned by the caller.
+ *    The library never frees or retains caller memory after a call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls are
+ *    stream-ordered and return after enqueueing, except where a stats pointer is given or the
+ *    name ends in `_host`: those synchronise the stream before returning.
+ *  - Errors are returned as of_status, never by aborting; of_last_error() gives the message of
+ *    the last non-OK status on the calling thread.
+ *  - An of_ctx may be used by one host thread at a time.
+ */
+#ifndef TVL1FLOW_H
+#define TVL1FLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct of_ctx of_ctx;
+
+typedef enum {
+    OF_OK = 0,
+    OF_EINVAL = 1,    /* invalid argument (sizes, pitches, parameters, NULL pointers) */
+    OF_ENOMEM = 2,    /* the device arena would exceed the context's HBM budget, or cudaMalloc failed */
+    OF_ECUDA = 3,     /* a CUDA runtime call failed (message names it) */
+    OF_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    OF_ENUMERIC = 5,  /* non-finite residual or energy (NaN/Inf input or parameters) */
+    OF_EBUSY = 6      /* the serving loop is not running / queue full */
+} of_status;
+
+typedef enum {
+    OF_PADMM_I = 0,   /* rpADMMI, Sec. 3.1.1 eq. (rpADMMI); r = 1 is pADMM; beta = 0 is Zach-pADMM */
+    OF_PADMM_II = 1,  /* rpADMMII, Sec. 3.1.1 eq. (rpADMMII) */
+    OF_PDR = 2        /* pDR, Sec. 3.1.2 eq. (pDR) with SRBGS preconditioner */
+} of_method;
+
+typedef enum { OF_PREC_FP32 = 0, OF_PREC_FP16 = 1, OF_PREC_BF16 = 2 } of_precision;
+
+typedef enum {
+    OF_ENGINE_FUSED = 0,  /* one fused kernel per inner iteration (default) */
+    OF_ENGINE_PLAIN = 1   /* one kernel per operator, FP32 only: the plain reference GPU path */
+} of_engine;
+
+/* Solver parameters.  Defaults (of_default_params) are the paper's Sec. 4 settings. */
+typedef struct {
+    int method;          /* of_method */
+    float lambda;        /* data weight lambda, |s| <= lambda (eq. ofc-dual)                  */
+    float beta;          /* illumination weight beta (eq. l1:optical:flow); 0 = beta = 0 model  */
+    float c;             /* ADMM penalty / step c (Sec. 4: 0.05)                               */
+    float a;             /* y-block preconditioner a, 1/a <= 1/||grad grad^*|| (Prop. 3.1: 8)    */
+    float a_tilde;       /* s-block preconditioner a~; <= 0 means ||M_s|| = max M_s per warp    */
+    float r;             /* rpADMMI relaxation r in (0, (1+sqrt 5)/2) (Sec. 4: 1 or 1.618)       */
+    float rho;           /* rpADMMII relaxation rho in (0, 2) (Sec. 4: 1.9)                     */
+    float sigma, tau;    /* pDR step sizes (Sec. 4: 2 and 0.4)                                  */
+    int gs_sweeps;       /* symmetric red-black Gauss-Seidel sweeps per pDR iteration (>= 1)    */
+    float eta;           /* pyramid scale factor in (0, 1)                                      */
+    int levels;          /* pyramid levels (1 = no pyramid), 1..16                              */
+    int warps;           /* warps (re-linearisations) per level, >= 1                          */
+    int iters;           /* inner iterations per warp, >= 0                                     */
+    double tol;          /* > 0: a warp's inner loop stops once the residual < tol, tested
+                            every 10 iterations; 0 = fixed schedule                            */
+    int precision;       /* of_precision: storage of the iterated fields; arithmetic is FP32   */
+    int fp32_last_warp;  /* 1: the finest level's last warp runs with FP32 storage             */
+    int engine;          /* of_engine                                                           */
+    int out_level;       /* stop after this pyramid level and return its flow (0 = finest)     */
+} of_params;
+
+typedef struct {
+    long long iters_run; /* inner iterations executed over the whole schedule                   */
+    double residual;     /* last residual: ||A s + B y|| / sqrt(rows) (ADMM) or
+                            ||X^{k+1} - X^k|| / sqrt(rows) (pDR), on the output level          */
+    double energy;       /* primal energy eq. (l1:finite) at the output level's last linearisation */
+    double dual_value;   /* <It, s> (eq. dual:l1:flow:cons); NaN for pDR                        */
+    float ms;            /* device time of the solve in milliseconds                            */
+} of_stats;
+
+/* Fills p with the paper's Sec. 4 settings: pADMM (r = 1), c = 0.05, a = 8, a~ = max M_s,
+ * rho = 1.9, sigma = 2, tau = 0.4, beta = 0.05, one SRBGS sweep; lambda = 0.05; eta = 0.5,
+ * 3 levels, 5 warps, 50 iterations; FP32, fused engine. */
+void of_default_params(of_params *p);
+
+/* Creates a context on CUDA device `device`.  The context owns one device arena that grows on
+ * demand up to `hbm_budget_bytes` (0 = 80% of the device's memory).  OF_EINVAL for a bad
+ * device, OF_ECUDA if the device cannot be used. */
+of_status of_create(of_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Releases the context, its arena and its cached CUDA graphs.  NULL is a no-op. */
+void of_destroy(of_ctx *ctx);
+
+/* Message of the last non-OK status returned on this thread (never NULL). */
+const char *of_last_error(of_ctx *ctx);
+
+/* Bytes of device arena a solve of an H x W pair with these parameters needs. */
+size_t of_arena_bytes(int H, int W, const of_params *params);
+
+/* Number of kernel launches one of_solve of an H x W pair with these parameters makes (the
+ * kernel nodes of its CUDA graph; captures the graph if it is not cached yet).  Returns -1 on
+ * error (message in of_last_error). */
+long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *params);
+
+/* Solves one pair (whole schedule: pyramid, levels, warps, inner iterations; Sec. 3-4).
+ * I0, I1: H x W FP32 images (device, pitch `pitch`).  u, v (and w unless NULL): outputs of size
+ * H_l x W_l at level params->out_level, FP32, pitch `out_pitch` (>= W_l).  stats: optional; if
+ * given the call synchronises `stream` and fills it.  The first call for a new (H, W, params)
+ * captures a CUDA graph that later calls replay. */
+of_status of_solve(of_ctx *ctx, const float *I0, const float *I1, int H, int W, int pitch,
+                   const of_params *params, float *u, float *v, float *w, int out_pitch,
+                   void *stream, of_stats *stats);
+
+/* As of_solve, but I0, I1, u, v, w are HOST pointers (dense, pitch = W resp. W_l); the
+ * host<->device copies run on `stream` inside the call, which returns after they finish. */
+of_status of_solve_host(of_ctx *ctx, const float *I0, const float *I1, int H, int W,
+                        const of_params *params, float *u, float *v, float *w,
+                        void *stream, of_stats *stats);
+
+/* Solves n independent pairs of possibly different sizes with one set of parameters.  Arrays
+ * of n device pointers / sizes; pitches in elements; w may be NULL (or entries NULL).  Pairs
+ * are processed together per pyramid level so that every launch covers all pairs.  stats: NULL
+ * or n entries (then the call synchronises).  Results equal n separate of_solve calls. */
+of_status of_solve_batch(of_ctx *ctx, int n, const float *const *I0, const float *const *I1,
+                         const int *H, const int *W, const int *pitch, const of_params *params,
+                         float *const *u, float *const *v, float *const *w, const int *out_pitch,
+                         void *stream, of_stats *stats);
+
+/* ---------------------------------------------------------------------------------------
+ * Step-level entry points: one row of the solver each, on caller-provided FP32 planes.  They
+ * exist so that each step can be checked on its own; of_solve chains the same kernels.
+ * All planes: device, H x W, pitch `pitch` elements unless stated.
+ * --------------------------------------------------------------------------------------- */
+
+/* Pyramid step (Sec. 4, reading: Gaussian pre-smoothing with sigma_g = 0.6 sqrt(eta^-2 - 1),
+ * radius ceil(3 sigma_g), half-sample symmetric border, then bilinear sampling at pixel
+ * centres).  fine: Hf x Wf (pitch pf) -> coarse: Hc x Wc (pitch pc).  scratch: >= Hf*pf floats. */
+of_status of_pyr_down(const float *fine, int Hf, int Wf, int pf, float *coarse, int Hc, int Wc,
+                      int pc, float eta, float *scratch, void *stream);
+
+/* Level transfer (Sec. 4 reading): bilinear upsampling of a field from Hc x Wc (pitch pc) to
+ * Hf x Wf (pitch pf), multiplied by `scale` (W_f/W_c for u, H_f/H_c for v, 1 for w). */
+of_status of_upsample(const float *coarse, int Hc, int Wc, int pc, float *fine, int Hf, int Wf,
+                      int pf, float scale, void *stream);
+
+/* Derivative images of I (Sec. 1 optical-flow constraint; reading: central differences with
+ * clamped indices). */
+of_status of_derivatives(const float *I, int H, int W, int pitch, float *Ix, float *Iy, void *stream);
+
+/* Warping and linearisation around d0 = (u0, v0): Ix, Iy = I1x, I1y sampled bilinearly at
+ * (x + u0, y + v0) clamped to the image, It = I1(x + d0) - I0 - Ix u0 - Iy v0.  ms_max: device
+ * pointer to one float that receives max(beta^2 + Ix^2 + Iy^2) (it must hold 0 or a smaller
+ * non-negative value on entry; the kernel raises it). */
+of_status of_warp_linearise(const float *I0, const float *I1, const float *I1x, const float *I1y,
+                            const float *u0, const float *v0, int H, int W, int pitch, float beta,
+                            float *Ix, float *Iy, float *It, float *ms_max, void *stream);
+
+/* Pointers to the iterated fields of one pair at one level (FP32 planes, shared pitch).
+ * ADMM: multipliers (w, u, v) and duals p = (p1, p2), q1 = (q11, q12), q2 = (q21, q22), s.
+ * pDR: X = (w, u, v), Xbar = (wb, ub, vb), ybar = (p, q); s unused.
+ * Components ending in 1 are x-components.  w, p1, p2, wb may be NULL when beta = 0. */
+typedef struct {
+    float *w, *u, *v, *p1, *p2, *q11, *q12, *q21, *q22, *s, *wb, *ub, *vb;
+} of_fields;
+
+/* `iters` inner iterations of rpADMMI / rpADMMII (params->method 0 or 1) at a fixed
+ * linearisation (Sec. 3.1.1), in place on `f`.  a_tilde > 0 is used as given.  The stopping
+ * rule params->tol applies.  res2: optional host pointer, receives ||A s + B y||^2 after the
+ * last iteration (synchronises).  Uses params->engine (FUSED or PLAIN); the fused engine
+ * needs `scratch`, a device buffer of >= of_fields_bytes(H, pitch) bytes (NULL for PLAIN). */
+of_status of_admm_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H,
+                          int W, int pitch, float a_tilde, const of_params *params, int iters,
+                          void *scratch, double *res2, void *stream);
+
+/* `iters` pDR iterations (Sec. 3.1.2) in place on `f`; res2: optional host pointer receiving
+ * ||X^{k+1} - X^k||^2 of the last iteration.  scratch as for of_admm_iterate. */
+of_status of_pdr_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H,
+                         int W, int pitch, const of_params *params, int iters, void *scratch,
+                         double *res2, void *stream);
+
+/* Scratch bytes the fused engine of the two calls above needs for an H-row plane set. */
+size_t of_fields_bytes(int H, int pitch);
+
+/* Primal energy eq. (l1:finite) and dual value <It, s> (eq. dual:l1:flow:cons) of FP32 fields,
+ * accumulated in FP64 on the device; results to host pointers (synchronises).  w and s may be
+ * NULL (then beta*w and the dual value are skipped / NaN). */
+of_status of_energy(const float *w, const float *u, const float *v, const float *s,
+                    const float *Ix, const float *Iy, const float *It, int H, int W, int pitch,
+                    float beta, float lambda, double *energy, double *dual_value, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving loop (continuous batching of requests of different sizes; no counterpart in the
+ * paper, which solves one pair at a time).
+ * --------------------------------------------------------------------------------------- */
+
+/* Starts the serving loop on the context with fixed parameters.  Requests are admitted while
+ * their arena bytes fit in `hbm_budget` (0 = the context budget) and at most `max_active` are
+ * on the device at once.  The loop runs on its own host thread and CUDA stream. */
+of_status of_server_start(of_ctx *ctx, const of_params *params, size_t hbm_budget, int max_active);
+
+/* Queues one request; I0, I1 are HOST float images (dense, pitch W) copied before return.
+ * *req_id receives the request id. */
+of_status of_server_submit(of_ctx *ctx, const float *I0, const float *I1, int H, int W, uint64_t *req_id);
+
+/* Polls a request.  *done = 1 when finished; then u, v (host, H x W dense, may be NULL) are
+ * filled, stats filled (may be NULL; ms = submit-to-finish latency), and the request retired. */
+of_status of_server_poll(of_ctx *ctx, uint64_t req_id, float *u, float *v, of_stats *stats, int *done);
+
+/* Stops the loop after the requests in flight finish; unfinished queued requests are dropped. */
+of_status of_server_stop(of_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TVL1FLOW_H */

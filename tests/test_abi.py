@@ -1,0 +1,55 @@
+"""CPU checks of the C ABI: the library loads, exports every function include/tvl1flow.h
+declares, and validates arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2011_10979_gb300 import build, flow
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return flow.lib()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(of_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert set(flow.EXPORTS) == names
+
+
+def test_default_params_are_the_papers(L):
+    p = flow.default_params()
+    assert (p.method, p.c, p.a, p.r, p.sigma, p.tau, p.gs_sweeps) == (0, pytest.approx(0.05), 8.0, 1.0, 2.0,
+                                                                      pytest.approx(0.4), 1)
+    assert p.rho == pytest.approx(1.9) and p.beta == pytest.approx(0.05) and p.eta == 0.5
+
+
+def test_arena_bytes_and_validation_without_gpu(L):
+    p = flow.default_params(levels=5, warps=10, iters=100)
+    n = L.of_arena_bytes(480, 640, ctypes.byref(p))
+    assert 20e6 < n < 200e6
+    for bad in (dict(levels=0), dict(eta=1.0), dict(lam=0.0), dict(r=1.7), dict(out_level=5)):
+        q = flow.default_params(**{"levels": 5, **bad})
+        assert L.of_arena_bytes(480, 640, ctypes.byref(q)) == 0
+    assert L.of_arena_bytes(0, 640, ctypes.byref(p)) == 0
+    st = L.of_solve(None, None, None, 10, 10, 10, ctypes.byref(p), None, None, None, 10, None, None)
+    assert st == flow.OF_EINVAL
+    assert b"ctx" in L.of_last_error(None)

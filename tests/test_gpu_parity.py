@@ -1,0 +1,296 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on the same seeded
+inputs.  Tolerances:
+  * single operators (pyramid, upsampling, derivatives, warping): FP32 rounding of O(1) values
+    over at most ~100 operations, bound 2e-5 absolute;
+  * inner iterations at a fixed linearisation: non-expansive iterations, FP32 rounding per step
+    ~1e-7 relative over tens of steps, bound 1e-4 absolute on O(1) fields;
+  * whole schedule: per pyramid level max|du|, max|dv| <= 1e-3 px and mean end-point error
+    <= 1e-2 px after the same schedule (the accuracy bar this library is built to).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2011_10979_gb300 import flow, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = flow.Context(0)
+    yield c
+    c.close()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def np64(t):
+    return t.detach().cpu().double().numpy()
+
+
+def _flow_errors(u, v, ru, rv):
+    du, dv = np.abs(u - ru), np.abs(v - rv)
+    return float(du.max()), float(dv.max()), float(np.hypot(u - ru, v - rv).mean())
+
+
+# ------------------------------------------------------------------------------- operators
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 5), (37, 53), (480, 640)])
+def test_pyr_down(ctx, orc, H, W):
+    img = np.random.default_rng(H + W).random((H, W)).astype(np.float32)
+    Hc, Wc = orc.level_size(H, 0.5), orc.level_size(W, 0.5)
+    got = np64(flow.of_pyr_down(cu(img), Hc, Wc, 0.5))
+    ref = orc.downsample(img.astype(np.float64), Hc, Wc, 0.5)
+    assert np.max(np.abs(got - ref)) < 2e-5
+
+
+@pytest.mark.parametrize("Hc,Wc,Hf,Wf", [(1, 1, 2, 2), (12, 16, 24, 32), (30, 40, 60, 80), (27, 55, 55, 109)])
+def test_upsample(ctx, orc, Hc, Wc, Hf, Wf):
+    f = np.random.default_rng(1).normal(size=(Hc, Wc)).astype(np.float32)
+    got = np64(flow.of_upsample(cu(f), Hf, Wf, Wf / Wc))
+    ref = orc.upsample(f.astype(np.float64), Hf, Wf, Wf / Wc)
+    assert np.max(np.abs(got - ref)) < 2e-5
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (7, 1), (45, 61)])
+def test_derivatives_and_warp(ctx, orc, H, W):
+    rng = np.random.default_rng(2)
+    I0, I1 = rng.random((H, W)).astype(np.float32), rng.random((H, W)).astype(np.float32)
+    u0 = rng.uniform(-5, 5, (H, W)).astype(np.float32)
+    v0 = rng.uniform(-5, 5, (H, W)).astype(np.float32)
+    gx, gy = flow.of_derivatives(cu(I1))
+    rx, ry = orc.derivatives(I1.astype(np.float64))
+    assert np.max(np.abs(np64(gx) - rx)) < 1e-6 and np.max(np.abs(np64(gy) - ry)) < 1e-6
+    Ix, Iy, It, ms = flow.of_warp_linearise(cu(I0), cu(I1), gx, gy, cu(u0), cu(v0), 0.05)
+    Rx, Ry, Rt, rms = orc.warp_linearise(I0, I1, np64(gx), np64(gy), u0, v0, 0.05)
+    for a, b in ((Ix, Rx), (Iy, Ry), (It, Rt)):
+        assert np.max(np.abs(np64(a) - b)) < 2e-5
+    assert abs(float(ms.item()) - rms) <= 1e-5 * rms
+
+
+# ------------------------------------------------------------------------------- iterations
+def _random_state(H, W, rng, lam, beta, pdr=False):
+    def ball(k):
+        x = rng.normal(size=(k, H, W))
+        return x / np.maximum(1.0, np.sqrt((x * x).sum(0)))
+    p, q = ball(2), ball(4)
+    st = dict(p1=p[0], p2=p[1], q11=q[0], q12=q[1], q21=q[2], q22=q[3])
+    for k in ("p1", "q11", "q21"):
+        st[k][:, -1] = 0.0
+    for k in ("p2", "q12", "q22"):
+        st[k][-1, :] = 0.0
+    st["s"] = rng.uniform(-lam, lam, (H, W))
+    for k in ("w", "u", "v", "wb", "ub", "vb"):
+        st[k] = rng.normal(size=(H, W))
+    if beta == 0.0:
+        for k in ("w", "p1", "p2", "wb"):
+            st[k] = np.zeros((H, W))
+    return {k: v.astype(np.float32) for k, v in st.items()}
+
+
+ITER_SHAPES = [(1, 1), (1, 9), (9, 1), (7, 5), (33, 17), (48, 64), (100, 130)]
+
+
+@pytest.mark.parametrize("H,W", ITER_SHAPES)
+@pytest.mark.parametrize("variant", ["padmm", "rpadmm1", "rpadmm2", "zach"])
+@pytest.mark.parametrize("engine", [flow.OF_ENGINE_FUSED, flow.OF_ENGINE_PLAIN])
+def test_admm_iterations(ctx, orc, H, W, variant, engine):
+    rng = np.random.default_rng(H * 31 + W)
+    lam, beta = 0.3, (0.0 if variant == "zach" else 0.05)
+    method = 1 if variant == "rpadmm2" else 0
+    r = 1.618 if variant == "rpadmm1" else 1.0
+    st = _random_state(H, W, rng, lam, beta)
+    Ix, Iy, It = (rng.normal(size=(H, W)).astype(np.float32) * s for s in (0.4, 0.4, 0.2))
+    at = float((beta ** 2 + Ix.astype(np.float64) ** 2 + Iy.astype(np.float64) ** 2).max()) + 1e-3
+    iters = 31
+    P = flow.default_params(method=method, lam=lam, beta=beta, r=r, rho=1.9, engine=engine)
+    fields = ("w", "u", "v", "p1", "p2", "q11", "q12", "q21", "q22", "s")
+    dev = {k: cu(st[k]) for k in fields}
+    if beta == 0.0:
+        for k in ("w", "p1", "p2"):
+            dev[k] = None
+    res_gpu = flow.of_admm_iterate(dev, cu(Ix), cu(Iy), cu(It), np.float32(at), P, iters)
+    ost = orc.State.zeros(H, W)
+    for k in orc.STATE_FIELDS:
+        ost[k] = st[k].astype(np.float64)
+    OP = orc.Params(method=method, lam=lam, beta=beta, r=r, rho=1.9)
+    for _ in range(iters):
+        res_ref = orc.admm_step(ost, Ix, Iy, It, float(np.float32(at)), OP)
+    for k in fields:
+        if dev[k] is None:
+            continue
+        err = np.max(np.abs(np64(dev[k]) - ost[k]))
+        assert err < 1e-4, (k, err)
+    assert abs(res_gpu - res_ref) <= 1e-3 * max(res_ref, 1e-6) + 1e-7
+
+
+@pytest.mark.parametrize("H,W", ITER_SHAPES)
+@pytest.mark.parametrize("beta", [0.05, 0.0])
+@pytest.mark.parametrize("engine", [flow.OF_ENGINE_FUSED, flow.OF_ENGINE_PLAIN])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_pdr_iterations(ctx, orc, H, W, beta, engine, sweeps):
+    rng = np.random.default_rng(H * 17 + W)
+    lam = 0.3
+    st = _random_state(H, W, rng, lam, beta, pdr=True)
+    Ix, Iy, It = (rng.normal(size=(H, W)).astype(np.float32) * s for s in (0.4, 0.4, 0.2))
+    iters = 23
+    P = flow.default_params(method=2, lam=lam, beta=beta, gs_sweeps=sweeps, engine=engine)
+    fields = ("w", "u", "v", "p1", "p2", "q11", "q12", "q21", "q22", "wb", "ub", "vb")
+    dev = {k: cu(st[k]) for k in fields}
+    if beta == 0.0:
+        for k in ("w", "p1", "p2", "wb"):
+            dev[k] = None
+    res_gpu = flow.of_pdr_iterate(dev, cu(Ix), cu(Iy), cu(It), P, iters)
+    ost = orc.State.zeros(H, W)
+    for k in orc.STATE_FIELDS:
+        if k in st:
+            ost[k] = st[k].astype(np.float64)
+    OP = orc.Params(method=2, lam=lam, beta=beta, gs_sweeps=sweeps)
+    for _ in range(iters):
+        res_ref = orc.pdr_step(ost, Ix, Iy, It, OP)
+    for k in fields:
+        if dev[k] is None:
+            continue
+        err = np.max(np.abs(np64(dev[k]) - ost[k]))
+        assert err < 1e-4, (k, err)
+    assert abs(res_gpu - res_ref) <= 1e-3 * max(res_ref, 1e-6) + 1e-7
+
+
+def test_energy(ctx, orc):
+    rng = np.random.default_rng(5)
+    H, W = 40, 50
+    a = {k: rng.normal(size=(H, W)).astype(np.float32) for k in ("w", "u", "v", "s", "Ix", "Iy", "It")}
+    e, d = flow.of_energy(*(cu(a[k]) for k in ("w", "u", "v", "s", "Ix", "Iy", "It")), 0.05, 0.7)
+    re = orc.energy(a["w"], a["u"], a["v"], a["Ix"], a["Iy"], a["It"], 0.05, 0.7)
+    rd = orc.dual_value(a["It"], a["s"])
+    assert abs(e - re) < 1e-5 * abs(re) and abs(d - rd) < 1e-5 * (abs(rd) + 1)
+
+
+# ------------------------------------------------------------------------------- whole schedule
+METHODS = {
+    "padmm": dict(method=0, r=1.0),
+    "rpadmm1": dict(method=0, r=1.618),
+    "rpadmm2": dict(method=1, rho=1.9),
+    "zach": dict(method=0, r=1.0, beta=0.0),
+    "pdr": dict(method=2),
+}
+
+
+def _solve_pair(ctx, orc, pr, levels, warps, iters, lam, extra, out_level=0, engine=flow.OF_ENGINE_FUSED):
+    kw = dict(lam=lam, levels=levels, warps=warps, iters=iters, out_level=out_level)
+    kw.update(extra)
+    P = flow.default_params(engine=engine, **kw)
+    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    OP = orc.Params(**{k: v for k, v in kw.items()})
+    ru, rv, _, rst = orc.solve(pr.I0, pr.I1, OP)
+    return np64(u), np64(v), ru, rv, st, rst
+
+
+@pytest.mark.parametrize("name", list(METHODS))
+@pytest.mark.parametrize("out_level", [0, 1, 2])
+def test_schedule_64x48_per_level(ctx, orc, name, out_level):
+    """The 64 x 48 sinusoid pair: 3 levels, 5 warps, 50 iterations, lambda = 0.05."""
+    pr = synth.sinusoid_pair()
+    u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 3, 5, 50, 0.05, METHODS[name], out_level)
+    mu, mv, epe = _flow_errors(u, v, ru, rv)
+    assert mu <= 1e-3 and mv <= 1e-3 and epe <= 1e-2, (mu, mv, epe)
+    assert st["iters_run"] == rst["iters_run"]
+    assert abs(st["energy"] - rst["energy"]) <= 1e-3 * rst["energy"]
+
+
+@pytest.mark.parametrize("name", list(METHODS))
+def test_schedule_64x48_strong_data_term(ctx, orc, name):
+    pr = synth.sinusoid_pair()
+    u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 3, 5, 50, 5.0, METHODS[name])
+    mu, mv, epe = _flow_errors(u, v, ru, rv)
+    assert mu <= 1e-3 and mv <= 1e-3 and epe <= 1e-2, (mu, mv, epe)
+    assert np.hypot(u - pr.u_true, v - pr.v_true).mean() < 0.1
+
+
+def test_plain_engine_matches_fused(ctx, orc):
+    pr = synth.sinusoid_pair()
+    out = []
+    for eng in (flow.OF_ENGINE_FUSED, flow.OF_ENGINE_PLAIN):
+        P = flow.default_params(lam=5.0, engine=eng)
+        u, v, _, _ = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+        out.append((np64(u), np64(v)))
+    assert np.max(np.abs(out[0][0] - out[1][0])) < 1e-4
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (6, 1), (3, 3), (17, 11)])
+def test_schedule_degenerate_sizes(ctx, orc, H, W):
+    rng = np.random.default_rng(H * 7 + W)
+    I0 = rng.random((H, W)).astype(np.float32)
+    I1 = np.roll(I0, 1, axis=1) if W > 1 else I0 * 0.9
+    pr = synth.Pair(I0, I1.astype(np.float32), None, None)
+    for name in ("padmm", "pdr"):
+        u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 3, 2, 7, 1.0, METHODS[name])
+        mu, mv, epe = _flow_errors(u, v, ru, rv)
+        assert mu <= 1e-3 and mv <= 1e-3, (name, mu, mv)
+
+
+def test_zero_iterations_and_identity_pair(ctx, orc):
+    pr = synth.sinusoid_pair()
+    P = flow.default_params(iters=0)
+    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    assert st["iters_run"] == 0 and float(u.abs().max()) == 0.0
+    P = flow.default_params()
+    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I0), P)
+    assert float(u.abs().max()) == 0.0 and float(v.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("name", ["padmm", "pdr"])
+def test_stopping_rule(ctx, orc, name):
+    pr = synth.sinusoid_pair()
+    extra = dict(METHODS[name], tol=3e-3)
+    u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 3, 5, 200, 5.0, extra)
+    assert st["iters_run"] < 3 * 5 * 200
+    assert abs(st["iters_run"] - rst["iters_run"]) <= 30, (st["iters_run"], rst["iters_run"])
+    if st["iters_run"] == rst["iters_run"]:
+        mu, mv, epe = _flow_errors(u, v, ru, rv)
+        assert mu <= 1e-3 and mv <= 1e-3
+
+
+def test_deterministic_and_host_entry(ctx):
+    pr = synth.sinusoid_pair(seed=3)
+    P = flow.default_params(lam=2.0)
+    a = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    b = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    hu, hv, _ = flow.of_solve_host(ctx, pr.I0, pr.I1, P)
+    assert np.array_equal(hu, a[0].cpu().numpy()) and np.array_equal(hv, a[1].cpu().numpy())
+
+
+def test_batch_equals_single(ctx):
+    pairs = [synth.sinusoid_pair(seed=s) for s in range(3)] + [synth.random_affine_rect_pair(64, 96, 7)]
+    P = flow.default_params(lam=2.0)
+    us, vs, sts = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], P)
+    for p, u, v in zip(pairs, us, vs):
+        su, sv, _, _ = flow.of_solve(ctx, cu(p.I0), cu(p.I1), P)
+        assert torch.equal(u, su) and torch.equal(v, sv)
+
+
+def test_invalid_arguments(ctx):
+    pr = synth.sinusoid_pair()
+    for bad in (dict(levels=0), dict(lam=-1.0), dict(eta=1.5), dict(method=7), dict(r=2.0),
+                dict(method=1, rho=2.5), dict(precision=1, engine=flow.OF_ENGINE_PLAIN), dict(out_level=3)):
+        with pytest.raises(flow.OfError) as e:
+            flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), flow.default_params(**bad))
+        assert e.value.status == flow.OF_EINVAL
+
+
+@pytest.mark.slow
+def test_schedule_640x480_full(ctx, orc):
+    """The 640 x 480 affine + box pair, whole schedule (5 levels, 10 warps, 100 iterations), pADMM,
+    every level against the oracle."""
+    pr = synth.affine_rect_pair()
+    for lvl in (4, 0):
+        u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 5, 10, 100, 5.0, METHODS["padmm"], out_level=lvl)
+        mu, mv, epe = _flow_errors(u, v, ru, rv)
+        assert mu <= 1e-3 and mv <= 1e-3 and epe <= 1e-2, (lvl, mu, mv, epe)
