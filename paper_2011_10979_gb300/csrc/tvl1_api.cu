@@ -579,6 +579,42 @@ of_status of_solve_host(of_ctx *ctx, const float *I0, const float *I1, int H, in
     return OF_OK;
 }
 
+}  // extern "C"
+
+int tvl1_solve_async(of_ctx *ctx, const float *I0, const float *I1, int H, int W, const void *params_v, float *u,
+                     float *v, cudaStream_t s) {
+    const of_params *params = (const of_params *)params_v;
+    of_status st = validate(params, H, W);
+    if (st != OF_OK) return st;
+    OF_CUDA(cudaSetDevice(ctx->device));
+    const Plan pl = make_plan(H, W, params);
+    st = ensure_arena(ctx, pl.total);
+    if (st != OF_OK) return st;
+    cudaGraphExec_t ge;
+    st = get_graph(ctx, pl, H, W, params, &ge);
+    if (st != OF_OK) return st;
+    char *A = ctx->arena;
+    OF_CUDA(cudaMemcpy2DAsync(A + pl.img0[0], (size_t)pl.P[0] * 4, I0, (size_t)W * 4, (size_t)W * 4, H,
+                              cudaMemcpyHostToDevice, s));
+    OF_CUDA(cudaMemcpy2DAsync(A + pl.img1[0], (size_t)pl.P[0] * 4, I1, (size_t)W * 4, (size_t)W * 4, H,
+                              cudaMemcpyHostToDevice, s));
+    OF_CUDA(cudaGraphLaunch(ge, s));
+    const int lo = pl.out_level;
+    const size_t on = (size_t)pl.H[lo] * pl.P[lo];
+    float *out = (float *)(A + pl.out);
+    OF_CUDA(cudaMemcpy2DAsync(u, (size_t)pl.W[lo] * 4, out, (size_t)pl.P[lo] * 4, (size_t)pl.W[lo] * 4, pl.H[lo],
+                              cudaMemcpyDeviceToHost, s));
+    OF_CUDA(cudaMemcpy2DAsync(v, (size_t)pl.W[lo] * 4, out + on, (size_t)pl.P[lo] * 4, (size_t)pl.W[lo] * 4,
+                              pl.H[lo], cudaMemcpyDeviceToHost, s));
+    return OF_OK;
+}
+
+size_t tvl1_ctx_bytes(of_ctx *ctx) { return ctx ? ctx->arena_bytes : 0; }
+
+void tvl1_set_error(const char *msg) { g_err = msg; }
+
+extern "C" {
+
 // ---------------------------------------------------------------- step-level entry points
 of_status of_pyr_down(const float *fine, int Hf, int Wf, int pf, float *coarse, int Hc, int Wc, int pc, float eta,
                       float *scratch, void *stream) {

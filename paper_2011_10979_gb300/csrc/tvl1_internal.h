@@ -103,3 +103,15 @@ void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, c
                        cudaStream_t s);
 
 }  // namespace tvl1
+
+// ---------------------------------------------------------------- runtime hooks (tvl1_api.cu)
+struct of_ctx;
+// Enqueues one solve on `s` without synchronising: host->device copy of I0/I1 (host pointers,
+// dense, pinned for asynchronous copies), the cached graph of the schedule, device->host copy of
+// u/v (dense, level params->out_level).  Validates and grows the context arena first.
+int tvl1_solve_async(of_ctx *ctx, const float *I0, const float *I1, int H, int W, const void *params,
+                     float *u, float *v, cudaStream_t s);
+// Device bytes the context currently holds (arena).
+size_t tvl1_ctx_bytes(of_ctx *ctx);
+// Sets the thread-local error message returned by of_last_error.
+void tvl1_set_error(const char *msg);

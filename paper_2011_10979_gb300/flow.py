@@ -113,6 +113,13 @@ def default_params(**kw) -> of_params:
     return p
 
 
+def out_size(H, W, params):
+    """Output size at params.out_level (1 x 1 when out_level is out of range: the C layer
+    rejects such parameters before touching the outputs)."""
+    sz = level_sizes(H, W, params.eta, max(1, params.levels))
+    return sz[params.out_level] if 0 <= params.out_level < len(sz) else (1, 1)
+
+
 def level_sizes(H, W, eta, levels):
     import math
     hs, ws = [H], [W]
@@ -160,7 +167,7 @@ def of_solve(ctx: Context, I0, I1, params: of_params, want_w=False, stats=True, 
     assert I0.is_cuda and I0.dtype == torch.float32 and I0.dim() == 2 and I0.stride(1) == 1
     assert I1.shape == I0.shape and I1.stride() == I0.stride() and I1.dtype == torch.float32
     H, W = I0.shape
-    h, w = level_sizes(H, W, params.eta, params.levels)[params.out_level]
+    h, w = out_size(H, W, params)
     u = torch.empty((h, w), dtype=torch.float32, device=I0.device)
     v = torch.empty_like(u)
     wo = torch.empty_like(u) if want_w else None
@@ -176,7 +183,7 @@ def of_solve_host(ctx: Context, I0, I1, params: of_params, stats=True, stream=No
     I0 = np.ascontiguousarray(I0, np.float32)
     I1 = np.ascontiguousarray(I1, np.float32)
     H, W = I0.shape
-    h, w = level_sizes(H, W, params.eta, params.levels)[params.out_level]
+    h, w = out_size(H, W, params)
     u = np.empty((h, w), np.float32)
     v = np.empty((h, w), np.float32)
     st = of_stats()
@@ -201,7 +208,7 @@ def of_solve_batch(ctx: Context, I0s, I1s, params: of_params, stats=True, stream
     us, vs = [], []
     for a in I0s:
         H, W = a.shape
-        h, w = level_sizes(H, W, params.eta, params.levels)[params.out_level]
+        h, w = out_size(H, W, params)
         us.append(torch.empty((h, w), dtype=torch.float32, device=a.device))
         vs.append(torch.empty((h, w), dtype=torch.float32, device=a.device))
     st = (of_stats * n)()

