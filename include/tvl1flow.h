@@ -185,6 +185,24 @@ of_status of_admm_iterate(of_fields f, const float *Ix, const float *Iy, const f
                           int W, int pitch, float a_tilde, const of_params *params, int iters,
                           void *scratch, double *res2, void *stream);
 
+/* Allocation-free form of of_admm_iterate with the fused engine.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory at all -- code running under a
+ * host allocator they do not control, inside a region where cudaMalloc would synchronise or is
+ * forbidden, or embedded in a runtime that owns every device byte.  Instead of a caller-provided
+ * `scratch` it uses one library-owned static device array of 32 MiB (every GPU that loads the
+ * library holds it until the process exits), so fields with of_fields_bytes(H, pitch) > 32 MiB
+ * are rejected with OF_EINVAL (640 x 480 FP32 fits).  The caller still passes every field and
+ * the linearisation data.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.  It calls
+ * no cudaMalloc/cudaFree.  All calls on a device share its one array, which keeps the last call's
+ * contents; each call clears what must start at zero, but two calls that overlap on the same GPU
+ * (e.g. issued on different streams) race on it: serialise them.  Arguments, results and errors
+ * are those of
+ * of_admm_iterate with params->engine forced to OF_ENGINE_FUSED. */
+of_status of_admm_iterate_noalloc(of_fields f, const float *Ix, const float *Iy, const float *It, int H,
+                                  int W, int pitch, float a_tilde, const of_params *params, int iters,
+                                  double *res2, void *stream);
+
 /* `iters` pDR iterations (Sec. 3.1.2) in place on `f`; res2: optional host pointer receiving
  * ||X^{k+1} - X^k||^2 of the last iteration.  scratch as for of_admm_iterate. */
 of_status of_pdr_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H,

@@ -23,7 +23,7 @@ OF_ENGINE_FUSED, OF_ENGINE_PLAIN = 0, 1
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
            "of_solve_kernel_count", "of_solve",
            "of_solve_host", "of_solve_batch", "of_pyr_down", "of_upsample", "of_derivatives",
-           "of_warp_linearise", "of_admm_iterate", "of_pdr_iterate", "of_fields_bytes", "of_energy",
+           "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_fields_bytes", "of_energy",
            "of_server_start", "of_server_submit", "of_server_poll", "of_server_stop")
 
 
@@ -84,6 +84,7 @@ def lib():
             "of_derivatives": (i, [vp, i, i, i, vp, vp, vp]),
             "of_warp_linearise": (i, [vp, vp, vp, vp, vp, vp, i, i, i, f, vp, vp, vp, vp, vp]),
             "of_admm_iterate": (i, [of_fields, vp, vp, vp, i, i, i, f, P(of_params), i, vp, P(d), vp]),
+            "of_admm_iterate_noalloc": (i, [of_fields, vp, vp, vp, i, i, i, f, P(of_params), i, P(d), vp]),
             "of_pdr_iterate": (i, [of_fields, vp, vp, vp, i, i, i, P(of_params), i, vp, P(d), vp]),
             "of_fields_bytes": (sz, [i, i]),
             "of_energy": (i, [vp, vp, vp, vp, vp, vp, vp, i, i, i, f, f, P(d), P(d), vp]),
