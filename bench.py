@@ -211,6 +211,9 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     t_plain = e0.elapsed_time(e1) / 3 / 1e3
+    batch = batch_measure(flow, torch, dev, fp32_flow=1)
+    batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
+    prec_line = precision_measure(flow, torch, dev)
     if rank != 0:
         return
     cpu = None
@@ -236,12 +239,89 @@ def run_ours(args):
             "plain_gpu": {"value": 1.0 / t_plain, "unit": "flows/s", "engine": "plain (one kernel per operator)",
                           "speedup": t_plain / t_step},
             "roofline": roof,
+            "batch": batch,
+            "batch_all16": batch_all16,
+            "precision_1024x436": prec_line,
             "cpu_baseline": cpu,
             "e2e": {"value": ws / t_e2e, "unit": "flows/s", "h2d_bytes_per_step": 2 * H * W * 4,
                     "d2h_bytes_per_step": 2 * H * W * 4},
             "gpu_launches": int(launches) * args.steps,
             "clocks": clocks}
     print(json.dumps(line), flush=True)
+
+
+def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, steps=2):
+    """Uneven-size batch: n pairs with sizes drawn uniformly from {96x64, 320x240, 640x480,
+    1024x436, 1242x375}, affine+box motion up to 15 px (`distinct` seeded pairs, each used
+    n/distinct times), BF16 storage, FP32 last warp, 5 levels x 10 warps x 100 iterations, solved
+    with of_solve_batch (one work-list launch per inner iteration for all pairs)."""
+    from paper_2011_10979_gb300 import synth
+    prec = flow.OF_PREC_BF16 if prec is None else prec
+    base = synth.batch_pairs(n=distinct)
+    pairs = [base[k % distinct] for k in range(n)]
+    I0 = [torch.from_numpy(p.I0).to(dev) for p in pairs]
+    I1 = [torch.from_numpy(p.I1).to(dev) for p in pairs]
+    P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
+                            precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow)
+    flow.of_solve_batch(flow_ctx_batch(flow, dev), I0, I1, P, stats=False)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        flow.of_solve_batch(flow_ctx_batch(flow, dev), I0, I1, P, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t = e0.elapsed_time(e1) / steps / 1e3
+    work = sum(mpix_iter_per_flow(h=p.I0.shape[0], w=p.I0.shape[1]) for p in pairs)   # Mpix*iter
+    bpp = 92.0 if prec == flow.OF_PREC_FP32 else (58.0 if fp32_flow else 46.0)
+    name = {0: "fp32", 1: "fp16", 2: "bf16"}[prec] + ("" if prec == flow.OF_PREC_FP32 else
+                                                        ("_duals+fp32_flow" if fp32_flow else "_all"))
+    return {"workload": "%d pairs uneven sizes (%d distinct seeded pairs), pADMM, 5x10x100" % (n, distinct),
+            "storage": name, "value": n / t, "unit": "flows/s",
+            "s_per_batch": t, "gpix_iter_per_s": work / 1e3 / t,
+            "effective_gbs": work * 1e6 * bpp / t / 1e9, "bytes_per_px_iter": bpp}
+
+
+_BATCH_CTX = {}
+
+
+def flow_ctx_batch(flow, dev):
+    if dev.index not in _BATCH_CTX:
+        _BATCH_CTX[dev.index] = flow.Context(dev.index)
+    return _BATCH_CTX[dev.index]
+
+
+def precision_measure(flow, torch, dev):
+    """The 1024 x 436 layered pair (6 levels x 10 warps x 150 iterations) with FP32, FP16 and BF16
+    storage (FP32 last warp): device time per solve and the EPE of the 16-bit results against
+    the FP32 result."""
+    from paper_2011_10979_gb300 import synth
+    pr = synth.layered_pair()
+    I0, I1 = torch.from_numpy(pr.I0).to(dev), torch.from_numpy(pr.I1).to(dev)
+    ctx = flow_ctx_batch(flow, dev)
+    out, ref = {}, None
+    for prec, ff, name in ((flow.OF_PREC_FP32, 1, "fp32"), (flow.OF_PREC_FP16, 1, "fp16_duals+fp32_flow"),
+                           (flow.OF_PREC_BF16, 1, "bf16_duals+fp32_flow"), (flow.OF_PREC_FP16, 0, "fp16_all"),
+                           (flow.OF_PREC_BF16, 0, "bf16_all")):
+        P = flow.default_params(lam=LAM, beta=BETA, levels=6, warps=10, iters=150, precision=prec, fp32_last_warp=1,
+                                fp32_flow=ff)
+        u, v, _, _ = flow.of_solve(ctx, I0, I1, P, stats=False)
+        torch.cuda.synchronize(dev)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            u, v, _, _ = flow.of_solve(ctx, I0, I1, P, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 3
+        if ref is None:
+            ref = (u.clone(), v.clone())
+        epe = float(torch.hypot(u - ref[0], v - ref[1]).mean())
+        out[name] = {"ms_per_solve": ms, "flows_per_s": 1e3 / ms, "epe_vs_fp32_px": epe,
+                     "max_abs_du_vs_fp32_px": float((u - ref[0]).abs().max())}
+    return out
 
 
 def kernel_roofline(flow, torch, dev, pr, iters=200):

@@ -78,6 +78,9 @@ typedef struct {
                             every 10 iterations; 0 = fixed schedule                            */
     int precision;       /* of_precision: storage of the iterated fields; arithmetic is FP32   */
     int fp32_last_warp;  /* 1: the finest level's last warp runs with FP32 storage             */
+    int fp32_flow;       /* 1: with 16-bit storage, keep the flow and illumination fields
+                            (w, u, v; pDR also its barred copies) in FP32 and store only the
+                            dual fields and the linearisation data in 16 bits               */
     int engine;          /* of_engine                                                           */
     int out_level;       /* stop after this pyramid level and return its flow (0 = finest)     */
 } of_params;
@@ -93,7 +96,8 @@ typedef struct {
 
 /* Fills p with the paper's Sec. 4 settings: pADMM (r = 1), c = 0.05, a = 8, a~ = max M_s,
  * rho = 1.9, sigma = 2, tau = 0.4, beta = 0.05, one SRBGS sweep; lambda = 0.05; eta = 0.5,
- * 3 levels, 5 warps, 50 iterations; FP32, fused engine. */
+ * 3 levels, 5 warps, 50 iterations; FP32, fused engine; with 16-bit storage, the last warp
+ * and the flow fields in FP32. */
 void of_default_params(of_params *p);
 
 /* Creates a context on CUDA device `device`.  The context owns one device arena that grows on

@@ -17,6 +17,44 @@ namespace {
 
 constexpr int PX = 32, PY = 8;
 
+// The planes one block works on: the single pair of the launch, or pair blockIdx.z of a batch.
+struct PView {
+    Geom g;
+    Fields f;
+    const void *Ix, *Iy, *It;
+    float *tmp;
+    const int *done;
+};
+
+__device__ __forceinline__ PView view_of(const IterArgs &A) {
+    // geometry in plain scalars from one 16-byte load per mode (see k_admm_fused.cu)
+    PView v;
+    if (A.pairs) {
+        const PairIter *pp = A.pairs + blockIdx.z;
+        const int4 gq = *reinterpret_cast<const int4 *>(&pp->g);
+        v.g.H = gq.x;
+        v.g.W = gq.y;
+        v.g.pitch = gq.z;
+        v.f = pp->buf[A.parity];
+        v.Ix = pp->Ix;
+        v.Iy = pp->Iy;
+        v.It = pp->It;
+        v.tmp = pp->tmp;
+        v.done = pp->done;
+    } else {
+        v.g.H = A.g.H;
+        v.g.W = A.g.W;
+        v.g.pitch = A.g.pitch;
+        v.f = A.in;
+        v.Ix = A.Ix;
+        v.Iy = A.Iy;
+        v.It = A.It;
+        v.tmp = A.tmp;
+        v.done = A.done;
+    }
+    return v;
+}
+
 template <typename T>
 __device__ __forceinline__ float div_at(const void *a, const void *b, int i, int j, int H, int W, int P) {
     const size_t o = (size_t)i * P + j;
@@ -29,59 +67,65 @@ __device__ __forceinline__ float div_at(const void *a, const void *b, int i, int
 }
 
 // b_c = Xbar_c + sigma div ybar_c, and a copy of X^k for the residual (FP32 planes in tmp).
-template <typename T>
-__global__ void k_pdr_b(IterArgs A, float *tmp, bool has_w) {
+template <typename T, typename TF>
+__global__ void k_pdr_b(IterArgs A, bool has_w) {
+    const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
-    const int H = A.g.H, W = A.g.W, P = A.g.pitch;
+    const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (i >= H || j >= W) return;
-    if (A.done && *A.done) return;
+    if (V.done && *V.done) return;
+    float *tmp = V.tmp;
     const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
     const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
     const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
     for (int c = has_w ? 0 : 1; c < 3; ++c) {
-        tmp[c * plane + o] = ldT<T>(A.in.f[XB[c]], o) + A.k.sigma * div_at<T>(A.in.f[Y1[c]], A.in.f[Y2[c]], i, j, H, W, P);
-        tmp[(3 + c) * plane + o] = ldT<T>(A.in.f[X[c]], o);
+        tmp[c * plane + o] = ldT<TF>(V.f.f[XB[c]], o) + A.k.sigma * div_at<T>(V.f.f[Y1[c]], V.f.f[Y2[c]], i, j, H, W, P);
+        tmp[(3 + c) * plane + o] = ldT<TF>(V.f.f[X[c]], o);
     }
 }
 
 // One red (colour 0) or black (colour 1) Gauss-Seidel half-sweep on (1 + st n_ij) x_ij - st sum x_nb = b_ij.
-template <typename T>
-__global__ void k_gs_half(IterArgs A, const float *tmp, int colour, bool has_w) {
+template <typename T, typename TF>
+__global__ void k_gs_half(IterArgs A, int colour, bool has_w) {
+    const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
-    const int H = A.g.H, W = A.g.W, P = A.g.pitch;
+    const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (i >= H || j >= W || ((i + j) & 1) != colour) return;
-    if (A.done && *A.done) return;
+    if (V.done && *V.done) return;
+    const float *tmp = V.tmp;
     const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
     const float st = A.k.sigma * A.k.tau;
     const int X[3] = {F_W, F_U, F_V};
     for (int c = has_w ? 0 : 1; c < 3; ++c) {
-        const void *x = A.in.f[X[c]];
+        const void *x = V.f.f[X[c]];
         float acc = 0.f;
         int nb = 0;
-        if (j > 0) { acc += ldT<T>(x, o - 1); ++nb; }
-        if (j < W - 1) { acc += ldT<T>(x, o + 1); ++nb; }
-        if (i > 0) { acc += ldT<T>(x, o - P); ++nb; }
-        if (i < H - 1) { acc += ldT<T>(x, o + P); ++nb; }
-        stT<T>(A.in.f[X[c]], o, (tmp[c * plane + o] + st * acc) / (1.f + st * (float)nb));
+        if (j > 0) { acc += ldT<TF>(x, o - 1); ++nb; }
+        if (j < W - 1) { acc += ldT<TF>(x, o + 1); ++nb; }
+        if (i > 0) { acc += ldT<TF>(x, o - P); ++nb; }
+        if (i < H - 1) { acc += ldT<TF>(x, o + P); ++nb; }
+        stT<TF>(V.f.f[X[c]], o, (tmp[c * plane + o] + st * acc) / (1.f + st * (float)nb));
     }
 }
 
 // Xbar update through the L1 resolvent, ybar update, residual partial ||X^{k+1} - X^k||^2.
-template <typename T>
-__global__ void k_pdr_finish(IterArgs A, const float *tmp, bool has_w) {
+template <typename T, typename TF>
+__global__ void k_pdr_finish(IterArgs A, bool has_w) {
     __shared__ double red[32];
+    const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
-    const int H = A.g.H, W = A.g.W, P = A.g.pitch;
-    if (A.done && *A.done) return;
+    const int H = V.g.H, W = V.g.W, P = V.g.pitch;
+    if (V.done && *V.done) return;
+    const float *tmp = V.tmp;
     double res = 0.0;
     if (i < H && j < W) {
         const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
         const float beta = A.k.beta, lam = A.k.lambda, sg = A.k.sigma, ta = A.k.tau;
-        const float ix = ldT<T>(A.Ix, o), iy = ldT<T>(A.Iy, o), it = ldT<T>(A.It, o);
-        const float xw = has_w ? ldT<T>(A.in.f[F_W], o) : 0.f;
-        const float xu = ldT<T>(A.in.f[F_U], o), xv = ldT<T>(A.in.f[F_V], o);
-        const float bw = has_w ? ldT<T>(A.in.f[F_WB], o) : 0.f;
-        const float bu = ldT<T>(A.in.f[F_UB], o), bv = ldT<T>(A.in.f[F_VB], o);
+        const float ix = ldT<T>(V.Ix, o), iy = ldT<T>(V.Iy, o), it = ldT<T>(V.It, o);
+        const float xw = has_w ? ldT<TF>(V.f.f[F_W], o) : 0.f;
+        const float xu = ldT<TF>(V.f.f[F_U], o), xv = ldT<TF>(V.f.f[F_V], o);
+        const float bw = has_w ? ldT<TF>(V.f.f[F_WB], o) : 0.f;
+        const float bu = ldT<TF>(V.f.f[F_UB], o), bv = ldT<TF>(V.f.f[F_VB], o);
         float zw = has_w ? 2.f * xw - bw : 0.f, zu = 2.f * xu - bu, zv = 2.f * xv - bv;
         const float e2 = beta * beta + ix * ix + iy * iy;
         const float rho = it + beta * zw + ix * zu + iy * zv;
@@ -93,27 +137,27 @@ __global__ void k_pdr_finish(IterArgs A, const float *tmp, bool has_w) {
         zw += t * beta;
         zu += t * ix;
         zv += t * iy;
-        if (has_w) stT<T>(A.in.f[F_WB], o, bw + zw - xw);
-        stT<T>(A.in.f[F_UB], o, bu + zu - xu);
-        stT<T>(A.in.f[F_VB], o, bv + zv - xv);
+        if (has_w) stT<TF>(V.f.f[F_WB], o, bw + zw - xw);
+        stT<TF>(V.f.f[F_UB], o, bu + zu - xu);
+        stT<TF>(V.f.f[F_VB], o, bv + zv - xv);
         const bool hx = j < W - 1, hy = i < H - 1;
-        auto gx = [&](int f, float x0) { return hx ? ldT<T>(A.in.f[f], o + 1) - x0 : 0.f; };
-        auto gy = [&](int f, float x0) { return hy ? ldT<T>(A.in.f[f], o + P) - x0 : 0.f; };
+        auto gx = [&](int f, float x0) { return hx ? ldT<TF>(V.f.f[f], o + 1) - x0 : 0.f; };
+        auto gy = [&](int f, float x0) { return hy ? ldT<TF>(V.f.f[f], o + P) - x0 : 0.f; };
         if (has_w) {
             const float g1 = gx(F_W, xw), g2 = gy(F_W, xw);
-            const float t1 = ldT<T>(A.in.f[F_P1], o) + 2.f * ta * g1, t2 = ldT<T>(A.in.f[F_P2], o) + 2.f * ta * g2;
+            const float t1 = ldT<T>(V.f.f[F_P1], o) + 2.f * ta * g1, t2 = ldT<T>(V.f.f[F_P2], o) + 2.f * ta * g2;
             const float f = fmaxf(1.f, sqrtf(t1 * t1 + t2 * t2));
-            stT<T>(A.in.f[F_P1], o, t1 / f - ta * g1);
-            stT<T>(A.in.f[F_P2], o, t2 / f - ta * g2);
+            stT<T>(V.f.f[F_P1], o, t1 / f - ta * g1);
+            stT<T>(V.f.f[F_P2], o, t2 / f - ta * g2);
         }
         const float ux = gx(F_U, xu), uy = gy(F_U, xu), vx = gx(F_V, xv), vy = gy(F_V, xv);
-        const float t11 = ldT<T>(A.in.f[F_Q11], o) + 2.f * ta * ux, t12 = ldT<T>(A.in.f[F_Q12], o) + 2.f * ta * uy;
-        const float t21 = ldT<T>(A.in.f[F_Q21], o) + 2.f * ta * vx, t22 = ldT<T>(A.in.f[F_Q22], o) + 2.f * ta * vy;
+        const float t11 = ldT<T>(V.f.f[F_Q11], o) + 2.f * ta * ux, t12 = ldT<T>(V.f.f[F_Q12], o) + 2.f * ta * uy;
+        const float t21 = ldT<T>(V.f.f[F_Q21], o) + 2.f * ta * vx, t22 = ldT<T>(V.f.f[F_Q22], o) + 2.f * ta * vy;
         const float f = fmaxf(1.f, sqrtf(t11 * t11 + t12 * t12 + t21 * t21 + t22 * t22));
-        stT<T>(A.in.f[F_Q11], o, t11 / f - ta * ux);
-        stT<T>(A.in.f[F_Q12], o, t12 / f - ta * uy);
-        stT<T>(A.in.f[F_Q21], o, t21 / f - ta * vx);
-        stT<T>(A.in.f[F_Q22], o, t22 / f - ta * vy);
+        stT<T>(V.f.f[F_Q11], o, t11 / f - ta * ux);
+        stT<T>(V.f.f[F_Q12], o, t12 / f - ta * uy);
+        stT<T>(V.f.f[F_Q21], o, t21 / f - ta * vx);
+        stT<T>(V.f.f[F_Q22], o, t22 / f - ta * vy);
         const float dw = has_w ? xw - tmp[3 * plane + o] : 0.f;
         const float du = xu - tmp[4 * plane + o], dv = xv - tmp[5 * plane + o];
         res = (double)dw * dw + (double)du * du + (double)dv * dv;
@@ -124,25 +168,25 @@ __global__ void k_pdr_finish(IterArgs A, const float *tmp, bool has_w) {
     }
 }
 
-template <typename T> void launch_pdr_t(const IterArgs &a, float *tmp6, bool literal, cudaStream_t s) {
+template <typename T, typename TF> void launch_pdr_t(const IterArgs &a, bool literal, cudaStream_t s) {
     const bool has_w = a.k.beta != 0.f;
-    dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + PY - 1) / PY), blk(PX, PY);
-    k_pdr_b<T><<<grid, blk, 0, s>>>(a, tmp6, has_w);
+    dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + PY - 1) / PY, a.pairs ? a.ntiles : 1), blk(PX, PY);
+    k_pdr_b<T, TF><<<grid, blk, 0, s>>>(a, has_w);
     if (literal) {
         for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
-            k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 0, has_w);
-            k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 1, has_w);
-            k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 1, has_w);
-            k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 0, has_w);
+            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
+            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
+            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
+            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
         }
     } else if (a.k.gs_sweeps > 0) {
-        k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 0, has_w);
+        k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
         for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
-            k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 1, has_w);
-            k_gs_half<T><<<grid, blk, 0, s>>>(a, tmp6, 0, has_w);
+            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
+            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
         }
     }
-    k_pdr_finish<T><<<grid, blk, 0, s>>>(a, tmp6, has_w);
+    k_pdr_finish<T, TF><<<grid, blk, 0, s>>>(a, has_w);
 }
 
 }  // namespace
@@ -150,10 +194,14 @@ template <typename T> void launch_pdr_t(const IterArgs &a, float *tmp6, bool lit
 int pdr_plain_blocks(Geom g) { return ((g.W + PX - 1) / PX) * ((g.H + PY - 1) / PY); }
 int pdr_fused_blocks(Geom g) { return pdr_plain_blocks(g); }
 
-void launch_pdr_plain(const IterArgs &a, cudaStream_t s) { launch_pdr_t<float>(a, a.tmp, true, s); }
+void launch_pdr_plain(const IterArgs &a, cudaStream_t s) { launch_pdr_t<float, float>(a, true, s); }
 
-void launch_pdr_fused(const IterArgs &a, int prec, cudaStream_t s) {
-    TVL1_DISPATCH_PREC(prec, T, launch_pdr_t<T>(a, a.tmp, false, s));
+void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
+    if (prec == PREC_F32) launch_pdr_t<float, float>(a, false, s);
+    else if (prec == PREC_F16 && prec_flow == PREC_F32) launch_pdr_t<__half, float>(a, false, s);
+    else if (prec == PREC_F16) launch_pdr_t<__half, __half>(a, false, s);
+    else if (prec_flow == PREC_F32) launch_pdr_t<__nv_bfloat16, float>(a, false, s);
+    else launch_pdr_t<__nv_bfloat16, __nv_bfloat16>(a, false, s);
 }
 
 }  // namespace tvl1

@@ -36,6 +36,33 @@ __device__ __forceinline__ float bilinear(const T *f, int H, int W, int P, float
     return (1.f - fy) * top + fy * bot;
 }
 
+// Sample position j + d clamped to [0, n-1], as integer part and fraction.  The fraction is taken
+// from d itself, so it keeps d's full precision however large j is.
+__device__ __forceinline__ void split_pos(int j, float d, int n, int &x0, float &fx) {
+    const float xs = (float)j + d;
+    if (!(xs > 0.f)) {              // also catches NaN
+        x0 = 0;
+        fx = 0.f;
+    } else if (xs >= (float)(n - 1)) {
+        x0 = n - 1;
+        fx = 0.f;
+    } else {
+        const float fl = floorf(d);
+        x0 = min(max(j + (int)fl, 0), n - 1);
+        fx = d - fl;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ float bilinear_split(const T *f, int H, int W, int P, int x0, float fx, int y0, float fy) {
+    const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
+    const float a = Store<T>::ld(f + (size_t)y0 * P + x0), b = Store<T>::ld(f + (size_t)y0 * P + x1);
+    const float c = Store<T>::ld(f + (size_t)y1 * P + x0), d = Store<T>::ld(f + (size_t)y1 * P + x1);
+    const float top = (1.f - fx) * a + fx * b;
+    const float bot = (1.f - fx) * c + fx * d;
+    return (1.f - fy) * top + fy * bot;
+}
+
 // Separable Gaussian, first along rows (x), then along columns (y); half-sample symmetric border.
 __global__ void k_blur_rows(const float *__restrict__ in, float *__restrict__ out, Geom g, GaussTaps t) {
     const int j = blockIdx.x * B2X + threadIdx.x, i = blockIdx.y * B2Y + threadIdx.y;
@@ -88,21 +115,23 @@ __global__ void k_derivatives(const float *__restrict__ I, Geom g, float *__rest
 // Warp I1 and its derivatives to (x + u0, y + v0) (clamped), linearise around d0:
 // It = I1w - I0 - Ix u0 - Iy v0, so that rho(w, d) = Ix u + Iy v + beta w + It.
 // The block max of M_s = beta^2 + Ix^2 + Iy^2 (of the stored, rounded values) raises *ms_max.
-template <typename T>
+template <typename T, typename TF>
 __global__ void k_warp(const float *__restrict__ I0, const float *__restrict__ I1, const float *__restrict__ I1x,
-                       const float *__restrict__ I1y, const T *__restrict__ u0, const T *__restrict__ v0, Geom g,
+                       const float *__restrict__ I1y, const TF *__restrict__ u0, const TF *__restrict__ v0, Geom g,
                        float beta, T *__restrict__ Ix, T *__restrict__ Iy, T *__restrict__ It, float *ms_max) {
     __shared__ float red[B2X * B2Y / 32];
     const int j = blockIdx.x * B2X + threadIdx.x, i = blockIdx.y * B2Y + threadIdx.y;
     float ms = 0.f;
     if (i < g.H && j < g.W) {
         const size_t o = (size_t)i * g.pitch + j;
-        const float uu = Store<T>::ld(u0 + o), vv = Store<T>::ld(v0 + o);
-        const float x = clampf((float)j + uu, 0.f, (float)(g.W - 1));
-        const float y = clampf((float)i + vv, 0.f, (float)(g.H - 1));
-        const float w1 = bilinear<float>(I1, g.H, g.W, g.pitch, x, y);
-        const float gx = bilinear<float>(I1x, g.H, g.W, g.pitch, x, y);
-        const float gy = bilinear<float>(I1y, g.H, g.W, g.pitch, x, y);
+        const float uu = Store<TF>::ld(u0 + o), vv = Store<TF>::ld(v0 + o);
+        int x0, y0;
+        float fx, fy;
+        split_pos(j, uu, g.W, x0, fx);
+        split_pos(i, vv, g.H, y0, fy);
+        const float w1 = bilinear_split<float>(I1, g.H, g.W, g.pitch, x0, fx, y0, fy);
+        const float gx = bilinear_split<float>(I1x, g.H, g.W, g.pitch, x0, fx, y0, fy);
+        const float gy = bilinear_split<float>(I1y, g.H, g.W, g.pitch, x0, fx, y0, fy);
         Store<T>::st(Ix + o, gx);
         Store<T>::st(Iy + o, gy);
         Store<T>::st(It + o, w1 - __ldg(I0 + o) - gx * uu - gy * vv);
@@ -183,11 +212,11 @@ void launch_derivatives(const float *I, Geom g, float *Ix, float *Iy, cudaStream
 
 void launch_warp(const float *I0, const float *I1, const float *I1x, const float *I1y, const void *u0,
                  const void *v0, Geom g, float beta, void *Ix, void *Iy, void *It, float *ms_max, int prec,
-                 cudaStream_t s) {
-    TVL1_DISPATCH_PREC(prec, T,
-                       k_warp<T><<<grid2(g.H, g.W), dim3(B2X, B2Y), 0, s>>>(
-                           I0, I1, I1x, I1y, (const T *)u0, (const T *)v0, g, beta, (T *)Ix, (T *)Iy, (T *)It,
-                           ms_max));
+                 int prec_flow, cudaStream_t s) {
+    TVL1_DISPATCH_PREC(prec, T, TVL1_DISPATCH_PREC(prec_flow, TF,
+                       k_warp<T, TF><<<grid2(g.H, g.W), dim3(B2X, B2Y), 0, s>>>(
+                           I0, I1, I1x, I1y, (const TF *)u0, (const TF *)v0, g, beta, (T *)Ix, (T *)Iy, (T *)It,
+                           ms_max)));
 }
 
 void launch_convert(const void *const *src, int src_prec, void *const *dst, int dst_prec, int nplanes, Geom g,

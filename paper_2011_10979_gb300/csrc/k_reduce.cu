@@ -40,7 +40,40 @@ __global__ void k_count_iters(long long *counter, const int *done, int n) {
     if (!(done && *done)) *counter += n;
 }
 
-template <typename T>
+// One block per pair: the stopping test (final = 0) or the final residual (final = 1).  A pair
+// that stopped keeps the residual of its stopping test.
+__global__ void k_reduce_check_batched(const double *partials, const PairScalars *ps, double tol, int add_iters,
+                                       int final) {
+    __shared__ double red[32];
+    const PairScalars P = ps[blockIdx.x];
+    const bool stopped = P.done && *P.done;
+    if (stopped && !final) return;
+    if (stopped) {
+        if (threadIdx.x == 0) *P.res_final = *P.res_check;
+        return;
+    }
+    double v = 0.0;
+    for (int k = P.part_begin + threadIdx.x; k < P.part_end; k += blockDim.x) v += partials[k];
+    const double tot = block_sum(v, red);
+    if (threadIdx.x == 0) {
+        if (final) {
+            *P.res_final = tot;
+        } else {
+            *P.res_check = tot;
+            if (P.iters) *P.iters += add_iters;
+            if (tol > 0.0 && sqrt(tot / P.rows) < tol) *P.done = 1;
+        }
+    }
+}
+
+__global__ void k_count_iters_batched(const PairScalars *ps, int npairs, int n, bool use_done) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npairs) return;
+    const PairScalars P = ps[k];
+    if (!(use_done && P.done && *P.done)) *P.iters += n;
+}
+
+template <typename T, typename TF>
 __global__ void k_energy(Fields f, const T *Ix, const T *Iy, const T *It, Geom g, float beta, float lambda,
                          double *pe, double *pd) {
     __shared__ double red[32];
@@ -51,7 +84,7 @@ __global__ void k_energy(Fields f, const T *Ix, const T *Iy, const T *It, Geom g
     if (i < H && j < W) {
         const size_t o = (size_t)i * P + j;
         const bool hx = j < W - 1, hy = i < H - 1;
-        auto L = [&](int fi, size_t off) { return ldT<T>(f.f[fi], off); };
+        auto L = [&](int fi, size_t off) { return is_flow_field(fi) ? ldT<TF>(f.f[fi], off) : ldT<T>(f.f[fi], off); };
         const float u = L(F_U, o), v = L(F_V, o);
         const float ux = hx ? L(F_U, o + 1) - u : 0.f, uy = hy ? L(F_U, o + P) - u : 0.f;
         const float vx = hx ? L(F_V, o + 1) - v : 0.f, vy = hy ? L(F_V, o + P) - v : 0.f;
@@ -75,14 +108,17 @@ __global__ void k_energy(Fields f, const T *Ix, const T *Iy, const T *It, Geom g
     }
 }
 
-template <typename T>
+template <typename T, typename TF>
 __global__ void k_parity_fix(Fields from, Fields to, Geom g, const int *done, int want_done) {
     if (((done && *done) ? 1 : 0) != want_done) return;
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
     if (i >= g.H || j >= g.W) return;
     const size_t o = (size_t)i * g.pitch + j;
-    for (int k = 0; k < NFIELDS; ++k)
-        if (from.f[k] && to.f[k]) reinterpret_cast<T *>(to.f[k])[o] = reinterpret_cast<const T *>(from.f[k])[o];
+    for (int k = 0; k < NFIELDS; ++k) {
+        if (!(from.f[k] && to.f[k])) continue;
+        if (is_flow_field(k)) reinterpret_cast<TF *>(to.f[k])[o] = reinterpret_cast<const TF *>(from.f[k])[o];
+        else reinterpret_cast<T *>(to.f[k])[o] = reinterpret_cast<const T *>(from.f[k])[o];
+    }
 }
 
 }  // namespace
@@ -98,20 +134,30 @@ void launch_count_iters(long long *counter, const int *done, int n, cudaStream_t
     k_count_iters<<<1, 1, 0, s>>>(counter, done, n);
 }
 
+void launch_reduce_check_batched(const double *partials, const PairScalars *ps, int npairs, double tol,
+                                 int add_iters, int final, cudaStream_t s) {
+    if (npairs > 0) k_reduce_check_batched<<<npairs, 256, 0, s>>>(partials, ps, tol, add_iters, final);
+}
+
+void launch_count_iters_batched(const PairScalars *ps, int npairs, int n, bool use_done, cudaStream_t s) {
+    if (npairs > 0) k_count_iters_batched<<<(npairs + 127) / 128, 128, 0, s>>>(ps, npairs, n, use_done);
+}
+
 int energy_blocks(Geom g) { return ((g.W + PX - 1) / PX) * ((g.H + PY - 1) / PY); }
 
 void launch_energy(const Fields &f, const void *Ix, const void *Iy, const void *It, Geom g, float beta, float lambda,
-                   int prec, double *pe, double *pd, cudaStream_t s) {
+                   int prec, int prec_flow, double *pe, double *pd, cudaStream_t s) {
     dim3 grid((g.W + PX - 1) / PX, (g.H + PY - 1) / PY), blk(PX, PY);
-    TVL1_DISPATCH_PREC(prec, T,
-                       k_energy<T><<<grid, blk, 0, s>>>(f, (const T *)Ix, (const T *)Iy, (const T *)It, g, beta,
-                                                        lambda, pe, pd));
+    TVL1_DISPATCH_PREC(prec, T, TVL1_DISPATCH_PREC(prec_flow, TF,
+                       k_energy<T, TF><<<grid, blk, 0, s>>>(f, (const T *)Ix, (const T *)Iy, (const T *)It, g, beta,
+                                                            lambda, pe, pd)));
 }
 
-void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, const int *done, int want_done,
-                       cudaStream_t s) {
+void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, int prec_flow, const int *done,
+                       int want_done, cudaStream_t s) {
     dim3 grid((g.W + PX - 1) / PX, (g.H + PY - 1) / PY), blk(PX, PY);
-    TVL1_DISPATCH_PREC(prec, T, k_parity_fix<T><<<grid, blk, 0, s>>>(from, to, g, done, want_done));
+    TVL1_DISPATCH_PREC(prec, T, TVL1_DISPATCH_PREC(prec_flow, TF,
+                       k_parity_fix<T, TF><<<grid, blk, 0, s>>>(from, to, g, done, want_done)));
 }
 
 }  // namespace tvl1

@@ -6,6 +6,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -45,10 +46,11 @@ int level_size(int n, float eta) {
 int pitch_of(int W) { return (int)align_up((size_t)W, 64); }
 
 struct Plan {
-    int L = 0, out_level = 0, prec = PREC_F32;
+    int L = 0, out_level = 0, prec = PREC_F32, pflow = PREC_F32;  // storage of duals/data, of w u v
     bool use32_last = false;
     int H[MAX_LEVELS], W[MAX_LEVELS], P[MAX_LEVELS];
     size_t plane32 = 0, planeT = 0;  // bytes of one finest-size plane in FP32 / storage precision
+    size_t planeS = 0;               // stride of the state planes (fits both storage types)
     size_t img0[MAX_LEVELS], img1[MAX_LEVELS];
     size_t I1x, I1y, blur, stA, stB, stA32, stB32, data, data32, tmp, partials, misc, out;
     int max_blocks = 0;
@@ -100,6 +102,7 @@ Plan make_plan(int H, int W, const of_params *p) {
     pl.L = p->levels;
     pl.out_level = p->out_level;
     pl.prec = p->precision;
+    pl.pflow = (p->precision != PREC_F32 && p->fp32_flow) ? PREC_F32 : p->precision;
     pl.use32_last = p->precision != PREC_F32 && p->fp32_last_warp && p->out_level == 0;
     pl.H[0] = H;
     pl.W[0] = W;
@@ -111,6 +114,7 @@ Plan make_plan(int H, int W, const of_params *p) {
     const size_t n0 = (size_t)pl.H[0] * pl.P[0];
     pl.plane32 = align_up(n0 * 4, 256);
     pl.planeT = align_up(n0 * prec_bytes(pl.prec), 256);
+    pl.planeS = align_up(n0 * std::max(prec_bytes(pl.prec), prec_bytes(pl.pflow)), 256);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -125,8 +129,8 @@ Plan make_plan(int H, int W, const of_params *p) {
     pl.I1x = take(pl.plane32);
     pl.I1y = take(pl.plane32);
     pl.blur = take(2 * pl.plane32);
-    pl.stA = take(NFIELDS * pl.planeT);
-    pl.stB = take(NFIELDS * pl.planeT);
+    pl.stA = take(NFIELDS * pl.planeS);
+    pl.stB = take(NFIELDS * pl.planeS);
     pl.data = take(3 * pl.planeT);
     if (pl.use32_last) {
         pl.stA32 = take(NFIELDS * pl.plane32);
@@ -220,153 +224,364 @@ Fields fields_at(char *base, size_t plane) {
 }
 
 // Enqueues the whole schedule of one pair on `s` (arena pointers only: graph-capturable).
-void enqueue_solve(of_ctx *ctx, const Plan &pl, const of_params *p, cudaStream_t s) {
-    char *A = ctx->arena;
-    Misc *misc = (Misc *)(A + pl.misc);
-    double *partials = (double *)(A + pl.partials);
-    const int mb = pl.max_blocks;
+// A batch of n pairs solved with one set of parameters.  Pair k owns the arena region
+// [base[k], base[k] + pl[k].total).  For n > 1 the arena also holds the tables of the batched
+// launches: per level the PairIter descriptors of all pairs (storage-precision buffers and, on
+// level 0 with the FP32 last warp, the FP32 buffers), the fused-ADMM tile work-list and the
+// per-pair scalars of the batched reductions, plus one partial-sum array shared by the batch.
+struct Batch {
+    int n = 0, L = 0, out_level = 0;
+    std::vector<Plan> pl;
+    std::vector<size_t> base;
+    size_t pairs_off[MAX_LEVELS][2] = {}, tiles_off[MAX_LEVELS] = {}, scal_off[MAX_LEVELS] = {};
+    int ntiles[MAX_LEVELS] = {}, tile_h[MAX_LEVELS] = {};
+    Geom gmax[MAX_LEVELS] = {};
+    size_t partials = 0, table_off = 0, table_bytes = 0, total = 0;
+    std::string key;
+};
+
+Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
+
+Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
+    Batch B;
+    B.n = n;
+    B.L = p->levels;
+    B.out_level = p->out_level;
+    size_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        B.pl.push_back(make_plan(H[k], W[k], p));
+        B.base.push_back(off);
+        off += align_up(B.pl.back().total, 256);
+    }
+    B.key.append((const char *)&n, sizeof(int));
+    for (int k = 0; k < n; ++k) {
+        B.key.append((const char *)&H[k], sizeof(int));
+        B.key.append((const char *)&W[k], sizeof(int));
+    }
+    of_params q;
+    memset(&q, 0, sizeof(q));
+    q = *p;
+    B.key.append((const char *)&q, sizeof(q));
+    if (n > 1) {
+        size_t t = 0, maxpart = 1;
+        const int SWD = admm_fused_strip_w(), NWP = admm_fused_warps();
+        for (int l = 0; l < B.L; ++l) {
+            long strip_rows = 0;
+            Geom gm{0, 0, 0};
+            for (int k = 0; k < n; ++k) {
+                const Geom g = geom_of(B.pl[k], l);
+                strip_rows += (long)((g.W + SWD - 1) / SWD) * g.H;
+                if (g.H > gm.H) gm.H = g.H;
+                if (g.W > gm.W) gm.W = g.W;
+            }
+            gm.pitch = pitch_of(gm.W);
+            B.gmax[l] = gm;
+            B.tile_h[l] = admm_fused_rows_per_warp(strip_rows);
+            const int rows = B.tile_h[l] * NWP;
+            int nt = 0;
+            for (int k = 0; k < n; ++k) {
+                const Geom g = geom_of(B.pl[k], l);
+                nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
+            }
+            B.ntiles[l] = nt;
+            B.pairs_off[l][0] = t;
+            t += align_up(sizeof(PairIter) * n, 256);
+            B.pairs_off[l][1] = t;
+            t += align_up(sizeof(PairIter) * n, 256);
+            B.tiles_off[l] = t;
+            t += align_up(sizeof(TileRef) * nt, 256);
+            B.scal_off[l] = t;
+            t += align_up(sizeof(PairScalars) * n, 256);
+            const size_t np = std::max((size_t)nt, (size_t)n * pdr_plain_blocks(gm));
+            maxpart = std::max(maxpart, np);
+        }
+        B.table_off = off;
+        B.table_bytes = t;
+        off += align_up(t, 256);
+        B.partials = off;
+        off += align_up(maxpart * sizeof(double), 256);
+    }
+    B.total = off;
+    return B;
+}
+
+// Writes the batched-launch tables (absolute device pointers into the current arena).
+of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
+    if (B.n <= 1) return OF_OK;
+    std::vector<char> img(B.table_bytes, 0);
+    const bool pdr = p->method == OF_PDR;
+    for (int l = 0; l < B.L; ++l) {
+        PairIter *pi0 = (PairIter *)(img.data() + B.pairs_off[l][0]);
+        PairIter *pi1 = (PairIter *)(img.data() + B.pairs_off[l][1]);
+        TileRef *tr = (TileRef *)(img.data() + B.tiles_off[l]);
+        PairScalars *ps = (PairScalars *)(img.data() + B.scal_off[l]);
+        int t = 0;
+        const int G = pdr_plain_blocks(B.gmax[l]);
+        for (int k = 0; k < B.n; ++k) {
+            const Plan &pl = B.pl[k];
+            char *A = ctx->arena + B.base[k];
+            Misc *misc = (Misc *)(A + pl.misc);
+            const Geom g = geom_of(pl, l);
+            for (int v = 0; v < 2; ++v) {
+                PairIter &P = v ? pi1[k] : pi0[k];
+                P.g = g;
+                if (v == 0) {
+                    P.buf[0] = fields_at(A + pl.stA, pl.planeS);
+                    P.buf[1] = fields_at(A + pl.stB, pl.planeS);
+                    P.Ix = A + pl.data;
+                    P.Iy = A + pl.data + pl.planeT;
+                    P.It = A + pl.data + 2 * pl.planeT;
+                } else {
+                    P.buf[0] = fields_at(A + pl.stA32, pl.plane32);
+                    P.buf[1] = fields_at(A + pl.stB32, pl.plane32);
+                    P.Ix = A + pl.data32;
+                    P.Iy = A + pl.data32 + pl.plane32;
+                    P.It = A + pl.data32 + 2 * pl.plane32;
+                }
+                P.ms_max = &misc->ms_max;
+                P.done = p->tol > 0.0 ? &misc->done : nullptr;
+                P.tmp = (float *)(A + pl.tmp);
+            }
+            const int rows = B.tile_h[l] * admm_fused_warps(), SWD = admm_fused_strip_w();
+            const int t0 = t;
+            for (int ty = 0; ty < (g.H + rows - 1) / rows; ++ty)
+                for (int tx = 0; tx < (g.W + SWD - 1) / SWD; ++tx) tr[t++] = TileRef{k, tx, ty, 0};
+            ps[k].res_check = &misc->res_check;
+            ps[k].res_final = &misc->res_final;
+            ps[k].done = &misc->done;
+            ps[k].iters = &misc->iters;
+            ps[k].rows = (double)g.H * g.W * (p->beta != 0.f ? 3.0 : 2.0);
+            ps[k].part_begin = pdr ? k * G : t0;
+            ps[k].part_end = pdr ? (k + 1) * G : t;
+        }
+    }
+    OF_CUDA(cudaMemcpy(ctx->arena + B.table_off, img.data(), img.size(), cudaMemcpyHostToDevice));
+    return OF_OK;
+}
+
+// Enqueues the whole schedule of every pair of the batch on `s` (arena pointers only: graph-
+// capturable).  Per pair: pyramid, level transfer, derivatives, warping, reductions.  The inner
+// iterations of all pairs go in one launch per iteration (a single pair: its own grid).
+void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t s) {
+    const int n = B.n;
+    const bool batched = n > 1;
     const bool has_w = p->beta != 0.f;
     const bool pdr = p->method == OF_PDR;
     const bool plain = p->engine == OF_ENGINE_PLAIN;
+    const bool pingpong = !pdr && !plain;
     const GaussTaps taps = gauss_taps(p->eta);
     const Coefs k = coefs_of(p);
-    cudaMemsetAsync(misc, 0, sizeof(Misc), s);
+    const int L = B.L;
+    double *bpart = batched ? (double *)(ctx->arena + B.partials) : nullptr;
 
-    auto geom = [&](int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; };
-    for (int l = 1; l < pl.L; ++l) {
-        launch_pyr_down((float *)(A + pl.img0[l - 1]), geom(l - 1), (float *)(A + pl.img0[l]), geom(l), taps,
-                        (float *)(A + pl.blur), s);
-        launch_pyr_down((float *)(A + pl.img1[l - 1]), geom(l - 1), (float *)(A + pl.img1[l]), geom(l), taps,
-                        (float *)(A + pl.blur), s);
+    struct PairCtx {
+        char *A;
+        const Plan *pl;
+        Misc *misc;
+        double *partials;
+        Fields buf[2], buf32[2];
+        const void *data[3], *data32[3];
+    };
+    std::vector<PairCtx> pc(n);
+    for (int q = 0; q < n; ++q) {
+        PairCtx &c = pc[q];
+        const Plan &pl = B.pl[q];
+        c.pl = &pl;
+        c.A = ctx->arena + B.base[q];
+        c.misc = (Misc *)(c.A + pl.misc);
+        c.partials = (double *)(c.A + pl.partials);
+        c.buf[0] = fields_at(c.A + pl.stA, pl.planeS);
+        c.buf[1] = fields_at(c.A + pl.stB, pl.planeS);
+        c.buf32[0] = fields_at(c.A + pl.stA32, pl.plane32);
+        c.buf32[1] = fields_at(c.A + pl.stB32, pl.plane32);
+        for (int d = 0; d < 3; ++d) {
+            c.data[d] = c.A + pl.data + d * pl.planeT;
+            c.data32[d] = c.A + pl.data32 + d * pl.plane32;
+        }
+        cudaMemsetAsync(c.misc, 0, sizeof(Misc), s);
+        for (int l = 1; l < L; ++l) {
+            launch_pyr_down((float *)(c.A + pl.img0[l - 1]), geom_of(pl, l - 1), (float *)(c.A + pl.img0[l]),
+                            geom_of(pl, l), taps, (float *)(c.A + pl.blur), s);
+            launch_pyr_down((float *)(c.A + pl.img1[l - 1]), geom_of(pl, l - 1), (float *)(c.A + pl.img1[l]),
+                            geom_of(pl, l), taps, (float *)(c.A + pl.blur), s);
+        }
     }
 
-    Fields buf[2] = {fields_at(A + pl.stA, pl.planeT), fields_at(A + pl.stB, pl.planeT)};
-    Fields buf32[2] = {fields_at(A + pl.stA32, pl.plane32), fields_at(A + pl.stB32, pl.plane32)};
-    int cur = 0;
-    int prec = pl.prec;
-    Fields *bufs = buf;
-    const void *data[3] = {A + pl.data, A + pl.data + pl.planeT, A + pl.data + 2 * pl.planeT};
-    const void *data32[3] = {A + pl.data32, A + pl.data32 + pl.plane32, A + pl.data32 + 2 * pl.plane32};
-    Geom last_g = geom(pl.L - 1);
+    int cur = 0, prec = B.pl[0].prec, pflow = B.pl[0].pflow;
+    bool in32 = false;  // the FP32 last-warp buffers are in use
+    auto bufs_of = [&](const PairCtx &c) { return in32 ? c.buf32 : c.buf; };
+    auto data_of = [&](const PairCtx &c) { return in32 ? c.data32 : c.data; };
 
-    for (int l = pl.L - 1; l >= pl.out_level; --l) {
-        const Geom g = geom(l);
-        last_g = g;
-        if (l == pl.L - 1) {
-            launch_fill(bufs[cur].f, prec, NFIELDS, g, 0.f, s);
-        } else {
-            const Geom gc = geom(l + 1);
-            const int nxt = cur ^ 1;
-            launch_upsample(bufs[cur].f[F_W], gc, bufs[nxt].f[F_W], g, 1.f, prec, s);
-            launch_upsample(bufs[cur].f[F_U], gc, bufs[nxt].f[F_U], g, (float)g.W / (float)gc.W, prec, s);
-            launch_upsample(bufs[cur].f[F_V], gc, bufs[nxt].f[F_V], g, (float)g.H / (float)gc.H, prec, s);
-            launch_fill(bufs[nxt].f + F_P1, prec, NFIELDS - F_P1, g, 0.f, s);
-            cur = nxt;
+    for (int l = L - 1; l >= B.out_level; --l) {
+        for (int q = 0; q < n; ++q) {
+            const PairCtx &c = pc[q];
+            const Plan &pl = *c.pl;
+            const Geom g = geom_of(pl, l);
+            const Fields *bf = bufs_of(c);
+            if (l == L - 1) {
+                launch_fill(bf[cur].f + F_W, pflow, 3, g, 0.f, s);
+            } else {
+                const Geom gc = geom_of(pl, l + 1);
+                const int nxt = cur ^ 1;
+                launch_upsample(bf[cur].f[F_W], gc, bf[nxt].f[F_W], g, 1.f, pflow, s);
+                launch_upsample(bf[cur].f[F_U], gc, bf[nxt].f[F_U], g, (float)g.W / (float)gc.W, pflow, s);
+                launch_upsample(bf[cur].f[F_V], gc, bf[nxt].f[F_V], g, (float)g.H / (float)gc.H, pflow, s);
+            }
+            const int now = l == L - 1 ? cur : cur ^ 1;
+            launch_fill(bf[now].f + F_P1, prec, F_S - F_P1 + 1, g, 0.f, s);   // duals p, q, s restart at 0
+            if (!has_w) launch_fill(bf[now].f + F_W, pflow, 1, g, 0.f, s);
+            if (pdr) {
+                const void *src[3] = {bf[now].f[F_W], bf[now].f[F_U], bf[now].f[F_V]};
+                void *dst[3] = {bf[now].f[F_WB], bf[now].f[F_UB], bf[now].f[F_VB]};
+                launch_copy_planes(src, dst, 3, g, pflow, s);
+            }
+            launch_derivatives((float *)(c.A + pl.img1[l]), g, (float *)(c.A + pl.I1x), (float *)(c.A + pl.I1y), s);
         }
-        if (!has_w) launch_fill(bufs[cur].f + F_W, prec, 1, g, 0.f, s);
-        if (pdr) {
-            const void *src[3] = {bufs[cur].f[F_W], bufs[cur].f[F_U], bufs[cur].f[F_V]};
-            void *dst[3] = {bufs[cur].f[F_WB], bufs[cur].f[F_UB], bufs[cur].f[F_VB]};
-            launch_copy_planes(src, dst, 3, g, prec, s);
-        }
-        launch_derivatives((float *)(A + pl.img1[l]), g, (float *)(A + pl.I1x), (float *)(A + pl.I1y), s);
-        const double rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
+        if (l != L - 1) cur ^= 1;
         for (int wp = 0; wp < p->warps; ++wp) {
-            const bool last_warp = (l == pl.out_level) && (wp == p->warps - 1);
-            const void *const *dat = data;
-            if (pl.use32_last && l == 0 && wp == p->warps - 1) {
-                // precision policy: the finest level's last warp runs with FP32 storage
-                launch_convert(bufs[cur].f, prec, buf32[0].f, PREC_F32, NFIELDS, g, s);
-                bufs = buf32;
+            const bool last_warp = (l == B.out_level) && (wp == p->warps - 1);
+            const bool switch32 = B.pl[0].use32_last && l == 0 && wp == p->warps - 1;
+            for (int q = 0; q < n; ++q) {
+                const PairCtx &c = pc[q];
+                const Plan &pl = *c.pl;
+                const Geom g = geom_of(pl, l);
+                if (switch32) {
+                    // precision policy: the finest level's last warp runs with FP32 storage
+                    launch_convert(c.buf[cur].f + F_W, pflow, c.buf32[0].f + F_W, PREC_F32, 3, g, s);
+                    launch_convert(c.buf[cur].f + F_P1, prec, c.buf32[0].f + F_P1, PREC_F32, F_S - F_P1 + 1, g, s);
+                    launch_convert(c.buf[cur].f + F_WB, pflow, c.buf32[0].f + F_WB, PREC_F32, 3, g, s);
+                }
+                const Fields *bf = switch32 ? c.buf32 : bufs_of(c);
+                const int cc = switch32 ? 0 : cur;
+                const void *const *dat = switch32 ? c.data32 : data_of(c);
+                const int pw = switch32 ? PREC_F32 : prec, pwf = switch32 ? PREC_F32 : pflow;
+                cudaMemsetAsync(&c.misc->ms_max, 0, sizeof(float) + sizeof(int), s);  // ms_max and done
+                launch_warp((float *)(c.A + pl.img0[l]), (float *)(c.A + pl.img1[l]), (float *)(c.A + pl.I1x),
+                            (float *)(c.A + pl.I1y), bf[cc].f[F_U], bf[cc].f[F_V], g, p->beta, (void *)dat[0],
+                            (void *)dat[1], (void *)dat[2], &c.misc->ms_max, pw, pwf, s);
+            }
+            if (switch32) {
+                in32 = true;
                 cur = 0;
                 prec = PREC_F32;
+                pflow = PREC_F32;
             }
-            if (prec == PREC_F32 && bufs == buf32) dat = data32;
-            cudaMemsetAsync(&misc->ms_max, 0, sizeof(float) + sizeof(int), s);  // ms_max and done
-            launch_warp((float *)(A + pl.img0[l]), (float *)(A + pl.img1[l]), (float *)(A + pl.I1x),
-                        (float *)(A + pl.I1y), bufs[cur].f[F_U], bufs[cur].f[F_V], g, p->beta, (void *)dat[0],
-                        (void *)dat[1], (void *)dat[2], &misc->ms_max, prec, s);
-            const bool pingpong = !pdr && !plain;
             const int start = cur;
             for (int it = 0; it < p->iters; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it == p->iters - 1;
-                IterArgs a;
-                a.g = g;
+                IterArgs a{};
                 a.k = k;
-                a.in = bufs[pingpong ? (start + it) & 1 : start];
-                a.out = bufs[pingpong ? (start + it + 1) & 1 : start];
-                a.Ix = dat[0];
-                a.Iy = dat[1];
-                a.It = dat[2];
-                a.ms_max = &misc->ms_max;
-                a.partials = (check || final_it) ? partials : nullptr;
-                a.done = p->tol > 0.0 ? &misc->done : nullptr;
-                a.tmp = (float *)(A + pl.tmp);
-                if (pdr) {
-                    if (plain) launch_pdr_plain(a, s);
-                    else launch_pdr_fused(a, prec, s);
+                if (!batched) {
+                    const PairCtx &c = pc[0];
+                    const Geom g = geom_of(*c.pl, l);
+                    const Fields *bf = bufs_of(c);
+                    const void *const *dat = data_of(c);
+                    a.g = g;
+                    a.in = bf[pingpong ? (start + it) & 1 : start];
+                    a.out = bf[pingpong ? (start + it + 1) & 1 : start];
+                    a.Ix = dat[0];
+                    a.Iy = dat[1];
+                    a.It = dat[2];
+                    a.ms_max = &c.misc->ms_max;
+                    a.partials = (check || final_it) ? c.partials : nullptr;
+                    a.done = p->tol > 0.0 ? &c.misc->done : nullptr;
+                    a.tmp = (float *)(c.A + c.pl->tmp);
+                    if (pdr) {
+                        if (plain) launch_pdr_plain(a, s);
+                        else launch_pdr_fused(a, prec, pflow, s);
+                    } else {
+                        if (plain) launch_admm_plain(a, s);
+                        else launch_admm_fused(a, prec, pflow, s);
+                    }
+                    if (check) {
+                        const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
+                        const double rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
+                        launch_reduce_check(c.partials, nb, &c.misc->res_check, rows, p->tol, &c.misc->done,
+                                            &c.misc->iters, 10, s);
+                    }
                 } else {
-                    if (plain) launch_admm_plain(a, s);
-                    else launch_admm_fused(a, prec, s);
-                }
-                if (check) {
-                    const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
-                    launch_reduce_check(partials, nb, &misc->res_check, rows, p->tol, &misc->done, &misc->iters, 10, s);
+                    a.pairs = (const PairIter *)(ctx->arena + B.table_off + B.pairs_off[l][in32 ? 1 : 0]);
+                    a.partials = (check || final_it) ? bpart : nullptr;
+                    if (pdr) {
+                        a.g = B.gmax[l];
+                        a.ntiles = n;
+                        a.parity = start;
+                        launch_pdr_fused(a, prec, pflow, s);
+                    } else {
+                        a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
+                        a.ntiles = B.ntiles[l];
+                        a.tile_h = B.tile_h[l];
+                        a.parity = (start + it) & 1;
+                        launch_admm_fused(a, prec, pflow, s);
+                    }
+                    if (check)
+                        launch_reduce_check_batched(bpart, (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]),
+                                                    n, p->tol, 10, 0, s);
                 }
             }
-            if (p->tol > 0.0) launch_count_iters(&misc->iters, &misc->done, p->iters % 10, s);
-            else launch_count_iters(&misc->iters, nullptr, p->iters, s);
+            const PairScalars *ps = batched ? (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]) : nullptr;
+            if (batched) {
+                launch_count_iters_batched(ps, n, p->tol > 0.0 ? p->iters % 10 : p->iters, p->tol > 0.0, s);
+            } else {
+                Misc *m = pc[0].misc;
+                if (p->tol > 0.0) launch_count_iters(&m->iters, &m->done, p->iters % 10, s);
+                else launch_count_iters(&m->iters, nullptr, p->iters, s);
+            }
             if (pingpong) {
                 const int fin = (start + p->iters) & 1;
-                if (p->tol > 0.0 && (p->iters & 1)) launch_parity_fix(bufs[start], bufs[fin], g, prec, &misc->done, 1, s);
+                if (p->tol > 0.0 && (p->iters & 1))
+                    for (int q = 0; q < n; ++q)
+                        launch_parity_fix(bufs_of(pc[q])[start], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l), prec,
+                                          pflow, &pc[q].misc->done, 1, s);
                 cur = fin;
             }
             if (last_warp && p->iters > 0) {
-                const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
-                launch_sum(partials, nb, &misc->res_final, s);
+                if (batched) {
+                    launch_reduce_check_batched(bpart, ps, n, 0.0, 0, 1, s);
+                } else {
+                    const Geom g = geom_of(*pc[0].pl, l);
+                    const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
+                    launch_sum(pc[0].partials, nb, &pc[0].misc->res_final, s);
+                }
             }
         }
-        if (l == pl.out_level) {
-            double *pe = partials + mb, *pd = partials + 2 * mb;
-            Fields fe = bufs[cur];
-            if (pdr) fe.f[F_S] = nullptr;
-            if (!has_w) fe.f[F_W] = nullptr;
-            const void *const *dat = (prec == PREC_F32 && bufs == buf32) ? data32 : data;
-            launch_energy(fe, dat[0], dat[1], dat[2], g, p->beta, p->lambda, prec, pe, pd, s);
-            launch_sum(pe, energy_blocks(g), &misc->energy, s);
-            launch_sum(pd, energy_blocks(g), &misc->dual, s);
-            Geom go = g;
-            float *out = (float *)(A + pl.out);
-            const size_t on = (size_t)pl.H[pl.out_level] * pl.P[pl.out_level];
-            const void *src[3] = {bufs[cur].f[F_U], bufs[cur].f[F_V], bufs[cur].f[F_W]};
-            void *dst[3] = {out, out + on, out + 2 * on};
-            launch_convert(src, prec, dst, PREC_F32, 3, go, s);
+        if (l == B.out_level) {
+            for (int q = 0; q < n; ++q) {
+                const PairCtx &c = pc[q];
+                const Plan &pl = *c.pl;
+                const Geom g = geom_of(pl, l);
+                const int mb = pl.max_blocks;
+                double *pe = c.partials + mb, *pd = c.partials + 2 * mb;
+                Fields fe = bufs_of(c)[cur];
+                if (pdr) fe.f[F_S] = nullptr;
+                if (!has_w) fe.f[F_W] = nullptr;
+                const void *const *dat = data_of(c);
+                launch_energy(fe, dat[0], dat[1], dat[2], g, p->beta, p->lambda, prec, pflow, pe, pd, s);
+                launch_sum(pe, energy_blocks(g), &c.misc->energy, s);
+                launch_sum(pd, energy_blocks(g), &c.misc->dual, s);
+                float *out = (float *)(c.A + pl.out);
+                const size_t on = (size_t)pl.H[pl.out_level] * pl.P[pl.out_level];
+                const void *src[3] = {bufs_of(c)[cur].f[F_U], bufs_of(c)[cur].f[F_V], bufs_of(c)[cur].f[F_W]};
+                void *dst[3] = {out, out + on, out + 2 * on};
+                launch_convert(src, pflow, dst, PREC_F32, 3, g, s);
+            }
         }
     }
-    (void)last_g;
 }
 
-std::string plan_key(int H, int W, const of_params *p) {
-    of_params q;
-    memset(&q, 0, sizeof(q));
-    q = *p;
-    std::string key((const char *)&H, sizeof(int));
-    key.append((const char *)&W, sizeof(int));
-    key.append((const char *)&q, sizeof(q));
-    return key;
-}
-
-of_status get_graph(of_ctx *ctx, const Plan &pl, int H, int W, const of_params *p, cudaGraphExec_t *out) {
-    const std::string key = plan_key(H, W, p);
-    auto it = ctx->graphs.find(key);
+of_status get_graph(of_ctx *ctx, const Batch &B, const of_params *p, cudaGraphExec_t *out, cudaGraph_t *graph_out = nullptr) {
+    auto it = ctx->graphs.find(B.key);
     if (it != ctx->graphs.end()) {
         *out = it->second.exec;
+        if (graph_out) *graph_out = it->second.graph;
         return OF_OK;
     }
+    of_status st = upload_tables(ctx, B, p);
+    if (st != OF_OK) return st;
     GraphEntry ge;
     OF_CUDA(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
-    enqueue_solve(ctx, pl, p, ctx->cap);
+    enqueue_solve(ctx, B, p, ctx->cap);
     cudaError_t e = cudaStreamEndCapture(ctx->cap, &ge.graph);
     if (e != cudaSuccess) return fail(OF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
@@ -374,14 +589,16 @@ of_status get_graph(of_ctx *ctx, const Plan &pl, int H, int W, const of_params *
         cudaGraphDestroy(ge.graph);
         return fail(OF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
     }
-    ctx->graphs[key] = ge;
+    ctx->graphs[B.key] = ge;
     *out = ge.exec;
+    if (graph_out) *graph_out = ge.graph;
     return OF_OK;
 }
 
-of_status read_stats(of_ctx *ctx, const Plan &pl, const of_params *p, cudaStream_t s, of_stats *stats) {
+of_status read_stats(of_ctx *ctx, const Batch &B, int q, const of_params *p, cudaStream_t s, of_stats *stats) {
+    const Plan &pl = B.pl[q];
     Misc m;
-    OF_CUDA(cudaMemcpyAsync(&m, ctx->arena + pl.misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
+    OF_CUDA(cudaMemcpyAsync(&m, ctx->arena + B.base[q] + pl.misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
     OF_CUDA(cudaStreamSynchronize(s));
     const Geom g{pl.H[pl.out_level], pl.W[pl.out_level], pl.P[pl.out_level]};
     const double rows = (double)g.H * g.W * (p->beta != 0.f ? 3.0 : 2.0);
@@ -420,6 +637,7 @@ void of_default_params(of_params *p) {
     p->tol = 0.0;
     p->precision = OF_PREC_FP32;
     p->fp32_last_warp = 1;
+    p->fp32_flow = 1;
     p->engine = OF_ENGINE_FUSED;
     p->out_level = 0;
 }
@@ -478,11 +696,11 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
     }
     if (validate(params, H, W) != OF_OK) return -1;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return -1;
-    const Plan pl = make_plan(H, W, params);
-    if (ensure_arena(ctx, pl.total) != OF_OK) return -1;
+    const Batch B = make_batch(1, &H, &W, params);
+    if (ensure_arena(ctx, B.total) != OF_OK) return -1;
     cudaGraphExec_t ge;
-    if (get_graph(ctx, pl, H, W, params, &ge) != OF_OK) return -1;
-    cudaGraph_t g = ctx->graphs[plan_key(H, W, params)].graph;
+    cudaGraph_t g;
+    if (get_graph(ctx, B, params, &ge, &g) != OF_OK) return -1;
     size_t n = 0;
     if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
     std::vector<cudaGraphNode_t> nodes(n);
@@ -495,118 +713,105 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
     return k;
 }
 
-of_status of_solve(of_ctx *ctx, const float *I0, const float *I1, int H, int W, int pitch, const of_params *params,
-                   float *u, float *v, float *w, int out_pitch, void *stream, of_stats *stats) {
+}  // extern "C"
+
+namespace {
+
+// Common body of the whole-solve entry points.  `host`: I0/I1/u/v/w are host pointers (dense)
+// and the copies go host<->device; otherwise device pointers with the given pitches.  `sync`:
+// wait for the stream before returning.
+of_status solve_pairs(of_ctx *ctx, int n, const float *const *I0, const float *const *I1, const int *H, const int *W,
+                      const int *pitch, const of_params *params, float *const *u, float *const *v, float *const *w,
+                      const int *out_pitch, bool host, void *stream, of_stats *stats, bool sync) {
     if (!ctx) return fail(OF_EINVAL, "ctx is NULL");
-    of_status st = validate(params, H, W);
-    if (st != OF_OK) return st;
-    if (!I0 || !I1 || !u || !v) return fail(OF_EINVAL, "NULL image or output pointer");
-    if (pitch < W) return fail(OF_EINVAL, "pitch < W");
+    if (n < 1) return fail(OF_EINVAL, "no pairs");
+    if (!params) return fail(OF_EINVAL, "params is NULL");
+    if (n > 1 && params->engine == OF_ENGINE_PLAIN)
+        return fail(OF_EINVAL, "batched solves use the fused engine (the plain engine is single-pair)");
+    for (int q = 0; q < n; ++q) {
+        of_status st = validate(params, H[q], W[q]);
+        if (st != OF_OK) return st;
+        if (!I0[q] || !I1[q] || !u[q] || !v[q]) return fail(OF_EINVAL, "NULL image or output pointer");
+        if (!host && pitch[q] < W[q]) return fail(OF_EINVAL, "pitch < W");
+    }
     OF_CUDA(cudaSetDevice(ctx->device));
-    const Plan pl = make_plan(H, W, params);
-    if (out_pitch < pl.W[pl.out_level]) return fail(OF_EINVAL, "out_pitch smaller than the output width");
-    st = ensure_arena(ctx, pl.total);
+    const Batch B = make_batch(n, H, W, params);
+    for (int q = 0; q < n; ++q)
+        if (!host && out_pitch[q] < B.pl[q].W[B.out_level]) return fail(OF_EINVAL, "out_pitch smaller than the output width");
+    of_status st = ensure_arena(ctx, B.total);
     if (st != OF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaGraphExec_t ge;
-    st = get_graph(ctx, pl, H, W, params, &ge);
+    st = get_graph(ctx, B, params, &ge);
     if (st != OF_OK) return st;
-    char *A = ctx->arena;
-    OF_CUDA(cudaMemcpy2DAsync(A + pl.img0[0], (size_t)pl.P[0] * 4, I0, (size_t)pitch * 4, (size_t)W * 4, H,
-                              cudaMemcpyDeviceToDevice, s));
-    OF_CUDA(cudaMemcpy2DAsync(A + pl.img1[0], (size_t)pl.P[0] * 4, I1, (size_t)pitch * 4, (size_t)W * 4, H,
-                              cudaMemcpyDeviceToDevice, s));
+    const cudaMemcpyKind kin = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const cudaMemcpyKind kout = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    for (int q = 0; q < n; ++q) {
+        const Plan &pl = B.pl[q];
+        char *A = ctx->arena + B.base[q];
+        const size_t sp = (size_t)(host ? W[q] : pitch[q]) * 4;
+        OF_CUDA(cudaMemcpy2DAsync(A + pl.img0[0], (size_t)pl.P[0] * 4, I0[q], sp, (size_t)W[q] * 4, H[q], kin, s));
+        OF_CUDA(cudaMemcpy2DAsync(A + pl.img1[0], (size_t)pl.P[0] * 4, I1[q], sp, (size_t)W[q] * 4, H[q], kin, s));
+    }
     if (stats) OF_CUDA(cudaEventRecord(ctx->ev0, s));
     OF_CUDA(cudaGraphLaunch(ge, s));
     if (stats) OF_CUDA(cudaEventRecord(ctx->ev1, s));
-    const int lo = pl.out_level;
-    const size_t on = (size_t)pl.H[lo] * pl.P[lo];
-    float *out = (float *)(A + pl.out);
-    float *dst[3] = {u, v, w};
-    for (int k = 0; k < 3; ++k)
-        if (dst[k])
-            OF_CUDA(cudaMemcpy2DAsync(dst[k], (size_t)out_pitch * 4, out + k * on, (size_t)pl.P[lo] * 4,
-                                      (size_t)pl.W[lo] * 4, pl.H[lo], cudaMemcpyDeviceToDevice, s));
-    if (stats) {
-        st = read_stats(ctx, pl, params, s, stats);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-        stats->ms = ms;
-        if (st != OF_OK) return st;
+    for (int q = 0; q < n; ++q) {
+        const Plan &pl = B.pl[q];
+        const int lo = pl.out_level;
+        const size_t on = (size_t)pl.H[lo] * pl.P[lo];
+        float *out = (float *)(ctx->arena + B.base[q] + pl.out);
+        float *dst[3] = {u[q], v[q], w ? w[q] : nullptr};
+        const size_t dp = (size_t)(host ? pl.W[lo] : out_pitch[q]) * 4;
+        for (int k = 0; k < 3; ++k)
+            if (dst[k])
+                OF_CUDA(cudaMemcpy2DAsync(dst[k], dp, out + k * on, (size_t)pl.P[lo] * 4, (size_t)pl.W[lo] * 4,
+                                          pl.H[lo], kout, s));
     }
+    if (stats) {
+        float ms = 0.f;
+        for (int q = 0; q < n; ++q) {
+            st = read_stats(ctx, B, q, params, s, stats + q);
+            if (q == 0) cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            stats[q].ms = ms;
+            if (st != OF_OK) return st;
+        }
+    }
+    if (sync) OF_CUDA(cudaStreamSynchronize(s));
     OF_CUDA(cudaGetLastError());
     return OF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+of_status of_solve(of_ctx *ctx, const float *I0, const float *I1, int H, int W, int pitch, const of_params *params,
+                   float *u, float *v, float *w, int out_pitch, void *stream, of_stats *stats) {
+    return solve_pairs(ctx, 1, &I0, &I1, &H, &W, &pitch, params, &u, &v, &w, &out_pitch, false, stream, stats, false);
+}
+
 of_status of_solve_host(of_ctx *ctx, const float *I0, const float *I1, int H, int W, const of_params *params,
                         float *u, float *v, float *w, void *stream, of_stats *stats) {
-    if (!ctx) return fail(OF_EINVAL, "ctx is NULL");
-    of_status st = validate(params, H, W);
-    if (st != OF_OK) return st;
-    if (!I0 || !I1 || !u || !v) return fail(OF_EINVAL, "NULL image or output pointer");
-    OF_CUDA(cudaSetDevice(ctx->device));
-    const Plan pl = make_plan(H, W, params);
-    st = ensure_arena(ctx, pl.total);
-    if (st != OF_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    cudaGraphExec_t ge;
-    st = get_graph(ctx, pl, H, W, params, &ge);
-    if (st != OF_OK) return st;
-    char *A = ctx->arena;
-    OF_CUDA(cudaMemcpy2DAsync(A + pl.img0[0], (size_t)pl.P[0] * 4, I0, (size_t)W * 4, (size_t)W * 4, H,
-                              cudaMemcpyHostToDevice, s));
-    OF_CUDA(cudaMemcpy2DAsync(A + pl.img1[0], (size_t)pl.P[0] * 4, I1, (size_t)W * 4, (size_t)W * 4, H,
-                              cudaMemcpyHostToDevice, s));
-    if (stats) OF_CUDA(cudaEventRecord(ctx->ev0, s));
-    OF_CUDA(cudaGraphLaunch(ge, s));
-    if (stats) OF_CUDA(cudaEventRecord(ctx->ev1, s));
-    const int lo = pl.out_level;
-    const size_t on = (size_t)pl.H[lo] * pl.P[lo];
-    float *out = (float *)(A + pl.out);
-    float *dst[3] = {u, v, w};
-    for (int k = 0; k < 3; ++k)
-        if (dst[k])
-            OF_CUDA(cudaMemcpy2DAsync(dst[k], (size_t)pl.W[lo] * 4, out + k * on, (size_t)pl.P[lo] * 4,
-                                      (size_t)pl.W[lo] * 4, pl.H[lo], cudaMemcpyDeviceToHost, s));
-    if (stats) {
-        st = read_stats(ctx, pl, params, s, stats);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-        stats->ms = ms;
-        if (st != OF_OK) return st;
-    }
-    OF_CUDA(cudaStreamSynchronize(s));
-    return OF_OK;
+    return solve_pairs(ctx, 1, &I0, &I1, &H, &W, &W, params, &u, &v, &w, &W, true, stream, stats, true);
+}
+
+of_status of_solve_batch(of_ctx *ctx, int n, const float *const *I0, const float *const *I1, const int *H,
+                         const int *W, const int *pitch, const of_params *params, float *const *u, float *const *v,
+                         float *const *w, const int *out_pitch, void *stream, of_stats *stats) {
+    if (n < 0 || (n > 0 && (!I0 || !I1 || !H || !W || !pitch || !u || !v || !out_pitch)))
+        return fail(OF_EINVAL, "of_solve_batch: NULL argument or n < 0");
+    if (n == 0) return OF_OK;
+    return solve_pairs(ctx, n, I0, I1, H, W, pitch, params, u, v, w, out_pitch, false, stream, stats, false);
 }
 
 }  // extern "C"
 
 int tvl1_solve_async(of_ctx *ctx, const float *I0, const float *I1, int H, int W, const void *params_v, float *u,
                      float *v, cudaStream_t s) {
-    const of_params *params = (const of_params *)params_v;
-    of_status st = validate(params, H, W);
-    if (st != OF_OK) return st;
-    OF_CUDA(cudaSetDevice(ctx->device));
-    const Plan pl = make_plan(H, W, params);
-    st = ensure_arena(ctx, pl.total);
-    if (st != OF_OK) return st;
-    cudaGraphExec_t ge;
-    st = get_graph(ctx, pl, H, W, params, &ge);
-    if (st != OF_OK) return st;
-    char *A = ctx->arena;
-    OF_CUDA(cudaMemcpy2DAsync(A + pl.img0[0], (size_t)pl.P[0] * 4, I0, (size_t)W * 4, (size_t)W * 4, H,
-                              cudaMemcpyHostToDevice, s));
-    OF_CUDA(cudaMemcpy2DAsync(A + pl.img1[0], (size_t)pl.P[0] * 4, I1, (size_t)W * 4, (size_t)W * 4, H,
-                              cudaMemcpyHostToDevice, s));
-    OF_CUDA(cudaGraphLaunch(ge, s));
-    const int lo = pl.out_level;
-    const size_t on = (size_t)pl.H[lo] * pl.P[lo];
-    float *out = (float *)(A + pl.out);
-    OF_CUDA(cudaMemcpy2DAsync(u, (size_t)pl.W[lo] * 4, out, (size_t)pl.P[lo] * 4, (size_t)pl.W[lo] * 4, pl.H[lo],
-                              cudaMemcpyDeviceToHost, s));
-    OF_CUDA(cudaMemcpy2DAsync(v, (size_t)pl.W[lo] * 4, out + on, (size_t)pl.P[lo] * 4, (size_t)pl.W[lo] * 4,
-                              pl.H[lo], cudaMemcpyDeviceToHost, s));
-    return OF_OK;
+    float *w = nullptr;
+    return solve_pairs(ctx, 1, &I0, &I1, &H, &W, &W, (const of_params *)params_v, &u, &v, &w, &W, true, (void *)s,
+                       nullptr, false);
 }
 
 size_t tvl1_ctx_bytes(of_ctx *ctx) { return ctx ? ctx->arena_bytes : 0; }
@@ -650,7 +855,7 @@ of_status of_warp_linearise(const float *I0, const float *I1, const float *I1x, 
                             float *ms_max, void *stream) {
     if (!I0 || !I1 || !I1x || !I1y || !u0 || !v0 || !Ix || !Iy || !It || !ms_max) return fail(OF_EINVAL, "NULL pointer");
     if (H < 1 || W < 1 || pitch < W) return fail(OF_EINVAL, "bad sizes or pitch");
-    launch_warp(I0, I1, I1x, I1y, u0, v0, Geom{H, W, pitch}, beta, Ix, Iy, It, ms_max, PREC_F32, (cudaStream_t)stream);
+    launch_warp(I0, I1, I1x, I1y, u0, v0, Geom{H, W, pitch}, beta, Ix, Iy, It, ms_max, PREC_F32, PREC_F32, (cudaStream_t)stream);
     OF_CUDA(cudaGetLastError());
     return OF_OK;
 }
@@ -717,7 +922,7 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
     const double rows = (double)H * W * (has_w ? 3.0 : 2.0);
     for (int it = 0; it < iters; ++it) {
         const bool check = params->tol > 0.0 && (it + 1) % 10 == 0;
-        IterArgs a;
+        IterArgs a{};
         a.g = g;
         a.k = k;
         a.in = bufs[pingpong ? it & 1 : 0];
@@ -731,10 +936,10 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
         a.tmp = tmp;
         if (pdr) {
             if (plain) launch_pdr_plain(a, s);
-            else launch_pdr_fused(a, PREC_F32, s);
+            else launch_pdr_fused(a, PREC_F32, PREC_F32, s);
         } else {
             if (plain) launch_admm_plain(a, s);
-            else launch_admm_fused(a, PREC_F32, s);
+            else launch_admm_fused(a, PREC_F32, PREC_F32, s);
         }
         if (check) {
             const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
@@ -747,7 +952,7 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
         Fields from = bufs[1], to = bufs[0];
         for (int q = 0; q < NFIELDS; ++q)
             if (!uf[q]) from.f[q] = to.f[q] = nullptr;
-        launch_parity_fix(from, to, g, PREC_F32, params->tol > 0.0 ? &misc->done : nullptr, 0, s);
+        launch_parity_fix(from, to, g, PREC_F32, PREC_F32, params->tol > 0.0 ? &misc->done : nullptr, 0, s);
     }
     if (res2) {
         const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
@@ -790,7 +995,7 @@ of_status of_energy(const float *w, const float *u, const float *v, const float 
     f.f[F_U] = (void *)u;
     f.f[F_V] = (void *)v;
     f.f[F_S] = (void *)s;
-    launch_energy(f, Ix, Iy, It, g, beta, lambda, PREC_F32, buf, buf + nb, st);
+    launch_energy(f, Ix, Iy, It, g, beta, lambda, PREC_F32, PREC_F32, buf, buf + nb, st);
     launch_sum(buf, nb, buf + 2 * nb, st);
     launch_sum(buf + nb, nb, buf + 2 * nb + 1, st);
     double h[2];

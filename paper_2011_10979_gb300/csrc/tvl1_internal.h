@@ -34,17 +34,59 @@ struct Coefs {
     int gs_sweeps;
 };
 
+// One pair at one level, for the batched (work-list) form of the fused engines: both ping-pong
+// state buffers, the linearisation data and the pair's device scalars.
+struct __align__(16) PairIter {
+    Geom g;  // read on the device as one 16-byte load (H, W, pitch, padding)
+    int pad_;
+    Fields buf[2];
+    const void *Ix, *Iy, *It;
+    const float *ms_max;
+    const int *done;
+    float *tmp;  // the pair's FP32 scratch planes (pDR engine)
+};
+
+// Device scalars of one pair in a batch, for the batched reductions: the partial sums of the
+// pair are partials[part_begin, part_end); rows normalises the residual.
+struct PairScalars {
+    double *res_check, *res_final;
+    int *done;
+    long long *iters;
+    int part_begin, part_end;
+    double rows;
+};
+
+// One work-list entry of a batched launch: pair index, tile column, tile row.
+struct TileRef {
+    int pair, tx, ty, pad;
+};
+
 // Per-iteration launch arguments of the ADMM / pDR engines.
 struct IterArgs {
-    Geom g;
-    Coefs k;
-    Fields in, out;                // fused engine: ping-pong buffers; plain engine: in == out
-    const void *Ix, *Iy, *It;      // linearisation data (same precision as the fields)
-    const float *ms_max;           // device max M_s of the current warp
-    double *partials;              // per-block residual partial sums, or nullptr
-    const int *done;               // early-exit flag of the current warp, or nullptr
-    float *tmp;                    // FP32 scratch planes (H x pitch each) for engines that need them
+    Geom g{};
+    Coefs k{};
+    Fields in{}, out{};            // fused engine: ping-pong buffers; plain engine: in == out
+    const void *Ix = nullptr, *Iy = nullptr, *It = nullptr;  // linearisation data (field precision)
+    const float *ms_max = nullptr; // device max M_s of the current warp
+    double *partials = nullptr;    // per-block residual partial sums, or nullptr
+    const int *done = nullptr;     // early-exit flag of the current warp, or nullptr
+    float *tmp = nullptr;          // FP32 scratch planes (H x pitch each) for engines that need them
+    // batched form (fused ADMM engine): when `tiles` is set, block b works on tiles[b] of pair
+    // pairs[tiles[b].pair], reads buf[parity] and writes buf[parity ^ 1]; g/in/out/Ix/Iy/It/
+    // ms_max/done above are ignored.  tile_h is the tile height the work-list was built for.
+    const PairIter *pairs = nullptr;
+    const TileRef *tiles = nullptr;
+    int ntiles = 0, parity = 0, tile_h = 0;
 };
+
+// Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w() output
+// columns and TY rows (TY = 1, 2, 8 or 32, chosen per level by admm_fused_tile_h); a block stacks
+// admm_fused_warps() strips vertically.  A work-list entry (pair, tx, ty) is the block covering
+// columns [tx * strip_w, ...) and rows [ty * warps * TY, ...).
+int admm_fused_tile_h(Geom g);
+int admm_fused_rows_per_warp(long strip_rows);   // strip_rows: sum over pairs of strips x rows
+int admm_fused_strip_w();
+int admm_fused_warps();
 
 // ---------------------------------------------------------------- pyramid / warp (k_pyramid.cu)
 constexpr int MAX_GAUSS_R = 16;
@@ -58,10 +100,10 @@ void launch_pyr_down(const float *fine, Geom gf, float *coarse, Geom gc, const G
 void launch_upsample(const void *coarse, Geom gc, void *fine, Geom gf, float scale, int prec, cudaStream_t s);
 void launch_upsample_f32(const float *coarse, Geom gc, float *fine, Geom gf, float scale, cudaStream_t s);
 void launch_derivatives(const float *I, Geom g, float *Ix, float *Iy, cudaStream_t s);
-// u0, v0 and the outputs Ix, Iy, It in precision `prec`; ms_max raised with atomicMax.
+// u0, v0 in precision `prec_flow`, the outputs Ix, Iy, It in `prec`; ms_max raised with atomicMax.
 void launch_warp(const float *I0, const float *I1, const float *I1x, const float *I1y, const void *u0,
                  const void *v0, Geom g, float beta, void *Ix, void *Iy, void *It, float *ms_max,
-                 int prec, cudaStream_t s);
+                 int prec, int prec_flow, cudaStream_t s);
 // Element-wise precision conversion of `nplanes` planes (same geometry).
 void launch_convert(const void *const *src, int src_prec, void *const *dst, int dst_prec, int nplanes,
                     Geom g, cudaStream_t s);
@@ -69,20 +111,22 @@ void launch_fill(void *const *dst, int prec, int nplanes, Geom g, float value, c
 void launch_copy_planes(const void *const *src, void *const *dst, int nplanes, Geom g, int prec, cudaStream_t s);
 
 // ---------------------------------------------------------------- ADMM (k_admm.cu)
-// Fused engine: one kernel per iteration, reads args.in, writes args.out.
+// Fused engine: one kernel per iteration, reads args.in, writes args.out.  The multipliers
+// (w, u, v) are stored in `prec_flow`, every other field and the linearisation data in `prec`.
 int admm_fused_blocks(Geom g);
-void launch_admm_fused(const IterArgs &a, int prec, cudaStream_t s);
+void launch_admm_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 // Plain engine (FP32): one kernel per operator, in place on args.in; args.tmp: 3 FP32 planes.
 int admm_plain_blocks(Geom g);
 void launch_admm_plain(const IterArgs &a, cudaStream_t s);
-// ||A s + B y||^2 partials of a state (for stats), per block.
-void launch_admm_residual(const Fields &f, const void *Ix, const void *Iy, Geom g, float beta, int prec,
-                          double *partials, cudaStream_t s);
 
 // ---------------------------------------------------------------- pDR (k_pdr.cu)
 // Both pDR engines work in place on args.in; args.tmp: 6 FP32 planes (b for w, u, v and X^k).
+// Batched form (args.pairs set, args.ntiles = number of pairs, args.g = the largest pair's
+// geometry): blockIdx.z selects the pair, its planes are pairs[z].buf[0] and pairs[z].tmp, and
+// its partials occupy pdr_plain_blocks(args.g) slots starting at z * pdr_plain_blocks(args.g).
 int pdr_fused_blocks(Geom g);
-void launch_pdr_fused(const IterArgs &a, int prec, cudaStream_t s);
+// X and Xbar (w u v wb ub vb) in `prec_flow`, ybar and the data in `prec`.
+void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 int pdr_plain_blocks(Geom g);
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s);
 
@@ -93,14 +137,21 @@ void launch_reduce_check(const double *partials, int n, double *out, double rows
                          long long *iters_counter, int add_iters, cudaStream_t s);
 int energy_blocks(Geom g);
 void launch_energy(const Fields &f, const void *Ix, const void *Iy, const void *It, Geom g, float beta,
-                   float lambda, int prec, double *partials_e, double *partials_d, cudaStream_t s);
+                   float lambda, int prec, int prec_flow, double *partials_e, double *partials_d, cudaStream_t s);
 void launch_sum(const double *partials, int n, double *out, cudaStream_t s);
 // Adds `n` to *counter unless *done is set.
 void launch_count_iters(long long *counter, const int *done, int n, cudaStream_t s);
+// Batched forms over `npairs` pairs (one block per pair): the stopping test on each pair's
+// partials (final = 0) or the final residual sum (final = 1, into res_final), and the counter.
+void launch_reduce_check_batched(const double *partials, const PairScalars *ps, int npairs, double tol,
+                                 int add_iters, int final, cudaStream_t s);
+void launch_count_iters_batched(const PairScalars *ps, int npairs, int n, bool use_done, cudaStream_t s);
 // Ping-pong parity repair: copies every non-NULL plane of `from` to `to` when the stop flag
 // state ((done && *done) ? 1 : 0) equals `want_done`.
-void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, const int *done, int want_done,
-                       cudaStream_t s);
+void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, int prec_flow, const int *done,
+                       int want_done, cudaStream_t s);
+// Whether field k is a flow/illumination plane (w u v wb ub vb), stored in the flow precision.
+__host__ __device__ inline bool is_flow_field(int k) { return k == F_W || k == F_U || k == F_V || k == F_WB || k == F_UB || k == F_VB; }
 
 }  // namespace tvl1
 

@@ -228,21 +228,6 @@ void tvl1_server_destroy(of_ctx *ctx) {
     if (S) destroy_server(S);
 }
 
-of_status of_solve_batch(of_ctx *ctx, int n, const float *const *I0, const float *const *I1, const int *H,
-                         const int *W, const int *pitch, const of_params *params, float *const *u, float *const *v,
-                         float *const *w, const int *out_pitch, void *stream, of_stats *stats) {
-    if (!ctx || n < 0 || (n > 0 && (!I0 || !I1 || !H || !W || !pitch || !u || !v || !out_pitch))) {
-        tvl1_set_error("of_solve_batch: NULL argument or n < 0");
-        return OF_EINVAL;
-    }
-    for (int k = 0; k < n; ++k) {
-        of_status st = of_solve(ctx, I0[k], I1[k], H[k], W[k], pitch[k], params, u[k], v[k], w ? w[k] : nullptr,
-                                out_pitch[k], stream, stats ? stats + k : nullptr);
-        if (st != OF_OK) return st;
-    }
-    return OF_OK;
-}
-
 of_status of_server_start(of_ctx *ctx, const of_params *params, size_t hbm_budget, int max_active) {
     if (!ctx || !params || max_active < 1 || max_active > 256) {
         tvl1_set_error("of_server_start: bad arguments (max_active in [1, 256])");

@@ -40,6 +40,7 @@ class of_params(ctypes.Structure):
                 ("tau", ctypes.c_float), ("gs_sweeps", ctypes.c_int), ("eta", ctypes.c_float),
                 ("levels", ctypes.c_int), ("warps", ctypes.c_int), ("iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_last_warp", ctypes.c_int),
+                ("fp32_flow", ctypes.c_int),
                 ("engine", ctypes.c_int), ("out_level", ctypes.c_int)]
 
 

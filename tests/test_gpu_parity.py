@@ -268,13 +268,32 @@ def test_deterministic_and_host_entry(ctx):
     assert np.array_equal(hu, a[0].cpu().numpy()) and np.array_equal(hv, a[1].cpu().numpy())
 
 
-def test_batch_equals_single(ctx):
-    pairs = [synth.sinusoid_pair(seed=s) for s in range(3)] + [synth.random_affine_rect_pair(64, 96, 7)]
-    P = flow.default_params(lam=2.0)
+BATCH_PAIRS = None
+
+
+def _batch_pairs():
+    global BATCH_PAIRS
+    if BATCH_PAIRS is None:
+        BATCH_PAIRS = ([synth.sinusoid_pair(seed=s) for s in range(3)] +
+                       [synth.random_affine_rect_pair(64, 96, 7), synth.random_affine_rect_pair(37, 53, 8),
+                        synth.random_affine_rect_pair(130, 100, 9),
+                        synth.Pair(np.full((1, 1), 0.5, np.float32), np.full((1, 1), 0.25, np.float32), None, None)])
+    return BATCH_PAIRS
+
+
+@pytest.mark.parametrize("name,prec,tol", [("padmm", 0, 0.0), ("rpadmm2", 0, 0.0), ("zach", 0, 0.0), ("pdr", 0, 0.0),
+                                           ("padmm", 2, 0.0), ("pdr", 1, 0.0), ("padmm", 0, 3e-3), ("pdr", 0, 3e-3)])
+def test_batch_equals_single(ctx, name, prec, tol):
+    """Uneven sizes solved in one batch (one work-list launch per iteration) give bitwise the
+    results of the separate single-pair solves."""
+    pairs = _batch_pairs()
+    P = flow.default_params(lam=2.0, precision=prec, tol=tol, iters=40, **METHODS[name])
     us, vs, sts = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], P)
-    for p, u, v in zip(pairs, us, vs):
-        su, sv, _, _ = flow.of_solve(ctx, cu(p.I0), cu(p.I1), P)
+    for p, u, v, st in zip(pairs, us, vs, sts):
+        su, sv, _, sst = flow.of_solve(ctx, cu(p.I0), cu(p.I1), P)
         assert torch.equal(u, su) and torch.equal(v, sv)
+        assert st["iters_run"] == sst["iters_run"]
+        assert st["energy"] == pytest.approx(sst["energy"], rel=1e-12, abs=1e-12)
 
 
 def test_invalid_arguments(ctx):
@@ -295,3 +314,40 @@ def test_schedule_640x480_full(ctx, orc):
         u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 5, 10, 100, 5.0, METHODS["padmm"], out_level=lvl)
         mu, mv, epe = _flow_errors(u, v, ru, rv)
         assert mu <= 1e-3 and mv <= 1e-3 and epe <= 1e-2, (lvl, mu, mv, epe)
+
+
+@pytest.mark.parametrize("prec", [flow.OF_PREC_FP16, flow.OF_PREC_BF16])
+@pytest.mark.parametrize("name", ["padmm", "pdr"])
+@pytest.mark.parametrize("fp32_flow", [1, 0])
+def test_precision_64x48(ctx, orc, prec, name, fp32_flow):
+    """16-bit storage with FP32 arithmetic and the finest level's last warp in FP32.  With the
+    flow fields kept in FP32 (duals and data in 16 bits) the end-point error against the FP64
+    oracle is <= 1e-2 px; storing the flow itself in 16 bits is reported and only bounded."""
+    pr = synth.sinusoid_pair()
+    kw = dict(lam=5.0, levels=3, warps=5, iters=50)
+    P = flow.default_params(precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, **kw, **METHODS[name])
+    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    ru, rv, _, _ = orc.solve(pr.I0, pr.I1, orc.Params(**kw, **METHODS[name]))
+    mu, mv, epe = _flow_errors(np64(u), np64(v), ru, rv)
+    print("prec %d fp32_flow %d %s: max|du| %.2e max|dv| %.2e EPE %.2e" % (prec, fp32_flow, name, mu, mv, epe))
+    assert epe <= (1e-2 if fp32_flow else 0.5), (mu, mv, epe)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,fp32_flow", [(flow.OF_PREC_FP32, 1), (flow.OF_PREC_FP16, 1), (flow.OF_PREC_BF16, 1),
+                                            (flow.OF_PREC_FP16, 0), (flow.OF_PREC_BF16, 0)])
+def test_precision_1024x436(ctx, orc, prec, fp32_flow):
+    """The 1024 x 436 layered pair (6 levels, 10 warps; 30 inner iterations to bound the oracle's
+    time) against the FP64 oracle: FP32, and 16-bit duals/data with FP32 flow fields, reach
+    EPE <= 1e-2 px; all-16-bit storage is reported."""
+    pr = synth.layered_pair()
+    kw = dict(lam=5.0, levels=6, warps=10, iters=30)
+    P = flow.default_params(precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, **kw)
+    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    ru, rv, _, _ = orc.solve(pr.I0, pr.I1, orc.Params(**kw))
+    mu, mv, epe = _flow_errors(np64(u), np64(v), ru, rv)
+    print("1024x436 prec %d fp32_flow %d: max|du| %.2e max|dv| %.2e EPE %.2e" % (prec, fp32_flow, mu, mv, epe))
+    if fp32_flow:
+        assert epe <= 1e-2, (mu, mv, epe)
+    if prec == flow.OF_PREC_FP32:
+        assert mu <= 1e-3 and mv <= 1e-3
