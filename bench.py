@@ -211,6 +211,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     t_plain = e0.elapsed_time(e1) / 3 / 1e3
+    serving = serving_measure(flow, torch, dev)
     batch = batch_measure(flow, torch, dev, fp32_flow=1)
     batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
     prec_line = precision_measure(flow, torch, dev)
@@ -240,6 +241,7 @@ def run_ours(args):
                           "speedup": t_plain / t_step},
             "roofline": roof,
             "batch": batch,
+            "serving": serving,
             "batch_all16": batch_all16,
             "precision_1024x436": prec_line,
             "cpu_baseline": cpu,
@@ -322,6 +324,56 @@ def precision_measure(flow, torch, dev):
         out[name] = {"ms_per_solve": ms, "flows_per_s": 1e3 / ms, "epe_vs_fp32_px": epe,
                      "max_abs_du_vs_fp32_px": float((u - ref[0]).abs().max())}
     return out
+
+
+def serving_measure(flow, torch, dev, rate_hz=20.0, duration_s=10.0, max_active=8):
+    """Serving loop under Poisson arrivals (rate_hz for duration_s), request sizes drawn from
+    {320x240: 40%, 640x480: 30%, 1024x436: 20%, 1920x1080: 8%, 3840x2160: 2%} with layered motion
+    up to 30 px (one seeded pair per size, reused), BF16 duals + FP32 flow, 5x10x100 schedule.
+    Latency = submit to result on the host; p50/p99 over all requests."""
+    from paper_2011_10979_gb300 import synth
+    imgs = {}
+    for (H, W), _ in synth.SERVE_MIX:
+        imgs[(H, W)] = synth.layered_pair(H, W, seed=40 + H, max_shift=30.0, sigma=0.01)
+    arrivals = synth.poisson_arrivals(rate_hz, duration_s, seed=5)
+    sizes = synth.serve_sizes(len(arrivals), seed=4)
+    P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
+                            precision=flow.OF_PREC_BF16, fp32_last_warp=1, fp32_flow=1)
+    ctx = flow.Context(dev.index)
+    flow.of_server_start(ctx, P, 0, max_active)
+    try:
+        # warm-up: one request per size captures each size's CUDA graph
+        warm = [(flow.of_server_submit(ctx, imgs[k].I0, imgs[k].I1), k) for k in imgs]
+        for rid, k in warm:
+            while flow.of_server_poll(ctx, rid, k) is None:
+                time.sleep(0.001)
+        pending, lat = {}, []
+        t0 = time.perf_counter()
+        nxt = 0
+        while nxt < len(arrivals) or pending:
+            now = time.perf_counter() - t0
+            while nxt < len(arrivals) and arrivals[nxt] <= now:
+                k = sizes[nxt]
+                pending[flow.of_server_submit(ctx, imgs[k].I0, imgs[k].I1)] = k
+                nxt += 1
+            for rid in list(pending):
+                r = flow.of_server_poll(ctx, rid, pending[rid])
+                if r is not None:
+                    lat.append(r[2])
+                    del pending[rid]
+            time.sleep(0.0005)
+        elapsed = time.perf_counter() - t0
+    finally:
+        flow.of_server_stop(ctx)
+        ctx.close()
+    lat = np.array(lat)
+    work = sum(mpix_iter_per_flow(h=h, w=w) for h, w in sizes)
+    return {"workload": "Poisson %.0f req/s for %.0f s, size mix 320x240..3840x2160, layered motion <= 30 px"
+                        % (rate_hz, duration_s),
+            "requests": int(len(lat)), "value": len(lat) / elapsed, "unit": "flows/s",
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "gpix_iter_per_s": work / 1e3 / elapsed, "max_active": max_active,
+            "storage": "bf16_duals+fp32_flow"}
 
 
 def kernel_roofline(flow, torch, dev, pr, iters=200):

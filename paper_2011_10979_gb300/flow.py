@@ -297,3 +297,38 @@ def of_energy(w, u, v, s, Ix, Iy, It, beta, lam, stream=None):
     check(lib().of_energy(_ptr(w), _ptr(u), _ptr(v), _ptr(s), _ptr(Ix), _ptr(Iy), _ptr(It), H, W, u.stride(0), beta,
                           lam, ctypes.byref(e), ctypes.byref(d), _stream(stream)))
     return e.value, d.value
+
+
+# ---------------------------------------------------------------------- serving loop
+def of_server_start(ctx: Context, params: of_params, hbm_budget: int = 0, max_active: int = 8):
+    check(lib().of_server_start(ctx.h, ctypes.byref(params), hbm_budget, max_active), ctx.h)
+
+
+def of_server_submit(ctx: Context, I0, I1) -> int:
+    """I0, I1: host float32 arrays (H x W).  Returns the request id."""
+    import numpy as np
+    I0 = np.ascontiguousarray(I0, np.float32)
+    I1 = np.ascontiguousarray(I1, np.float32)
+    H, W = I0.shape
+    rid = ctypes.c_uint64(0)
+    check(lib().of_server_submit(ctx.h, I0.ctypes.data_as(ctypes.c_void_p), I1.ctypes.data_as(ctypes.c_void_p), H, W,
+                                 ctypes.byref(rid)), ctx.h)
+    return rid.value
+
+
+def of_server_poll(ctx: Context, rid: int, shape):
+    """Returns None while the request runs, else (u, v, latency_ms) as host arrays; raises the
+    request's error status if it failed."""
+    import numpy as np
+    h, w = shape
+    u = np.empty((h, w), np.float32)
+    v = np.empty((h, w), np.float32)
+    st = of_stats()
+    done = ctypes.c_int(0)
+    check(lib().of_server_poll(ctx.h, ctypes.c_uint64(rid), u.ctypes.data_as(ctypes.c_void_p),
+                               v.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st), ctypes.byref(done)), ctx.h)
+    return (u, v, st.ms) if done.value else None
+
+
+def of_server_stop(ctx: Context):
+    check(lib().of_server_stop(ctx.h), ctx.h)
