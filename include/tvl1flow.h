@@ -54,8 +54,14 @@ typedef enum {
 typedef enum { OF_PREC_FP32 = 0, OF_PREC_FP16 = 1, OF_PREC_BF16 = 2 } of_precision;
 
 typedef enum {
-    OF_ENGINE_FUSED = 0,  /* one fused kernel per inner iteration (default) */
-    OF_ENGINE_PLAIN = 1   /* one kernel per operator, FP32 only: the plain reference GPU path */
+    OF_ENGINE_FUSED = 0,    /* default: small levels (those the level-resident launch runs faster)
+                               run all inner iterations of a warp in one level-resident launch of
+                               a thread-block cluster; the others one fused streaming kernel per
+                               inner iteration.  Both give bitwise the same flow. */
+    OF_ENGINE_PLAIN = 1,    /* one kernel per operator, FP32 only: the plain reference GPU path */
+    OF_ENGINE_STREAM = 2,   /* the fused streaming kernel on every level */
+    OF_ENGINE_RESIDENT = 3  /* the level-resident launch on every level that fits one cluster's
+                               shared memory, the streaming kernel on the others */
 } of_engine;
 
 /* Solver parameters.  Defaults (of_default_params) are the paper's Sec. 4 settings. */
@@ -183,7 +189,8 @@ typedef struct {
 /* `iters` inner iterations of rpADMMI / rpADMMII (params->method 0 or 1) at a fixed
  * linearisation (Sec. 3.1.1), in place on `f`.  a_tilde > 0 is used as given.  The stopping
  * rule params->tol applies.  res2: optional host pointer, receives ||A s + B y||^2 after the
- * last iteration (synchronises).  Uses params->engine (FUSED or PLAIN); the fused engine
+ * last iteration (synchronises).  Uses params->engine: PLAIN, or the fused streaming kernel
+ * (FUSED and STREAM alike: this call has no level-resident form); the fused kernel
  * needs `scratch`, a device buffer of >= of_fields_bytes(H, pitch) bytes (NULL for PLAIN). */
 of_status of_admm_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H,
                           int W, int pitch, float a_tilde, const of_params *params, int iters,

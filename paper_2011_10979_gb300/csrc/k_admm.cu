@@ -7,7 +7,7 @@
 // A s + B y = (beta s - div p, I_x s - div q1, I_y s - div q2).
 //
 // This file holds the plain engine -- one kernel per operator (div, y-update, div, s/multiplier
-// update) in FP32, in place; the fused engine is k_admm_fused.cu.
+// update) in FP32, in place; the fused engine is k_admm_roll.cuh.
 #include <math.h>
 
 #include "tvl1_device.cuh"

@@ -27,7 +27,7 @@ struct PView {
 };
 
 __device__ __forceinline__ PView view_of(const IterArgs &A) {
-    // geometry in plain scalars from one 16-byte load per mode (see k_admm_fused.cu)
+    // geometry in plain scalars from one 16-byte load per mode (as in k_admm_roll.cuh)
     PView v;
     if (A.pairs) {
         const PairIter *pp = A.pairs + blockIdx.z;

@@ -46,6 +46,7 @@ __global__ void k_reduce_check_batched(const double *partials, const PairScalars
                                        int final) {
     __shared__ double red[32];
     const PairScalars P = ps[blockIdx.x];
+    if (P.resident) return;  // the level-resident engine keeps this pair's scalars itself
     const bool stopped = P.done && *P.done;
     if (stopped && !final) return;
     if (stopped) {
@@ -70,7 +71,7 @@ __global__ void k_count_iters_batched(const PairScalars *ps, int npairs, int n, 
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npairs) return;
     const PairScalars P = ps[k];
-    if (!(use_done && P.done && *P.done)) *P.iters += n;
+    if (!P.resident && !(use_done && P.done && *P.done)) *P.iters += n;
 }
 
 template <typename T, typename TF>

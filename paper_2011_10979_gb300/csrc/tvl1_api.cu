@@ -90,7 +90,7 @@ of_status validate(const of_params *p, int H, int W) {
     if (p->iters < 0) return fail(OF_EINVAL, "iters must be >= 0");
     if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(OF_EINVAL, "tol must be >= 0");
     if (p->precision < 0 || p->precision > 2) return fail(OF_EINVAL, "unknown precision");
-    if (p->engine < 0 || p->engine > 1) return fail(OF_EINVAL, "unknown engine");
+    if (p->engine < 0 || p->engine > 3) return fail(OF_EINVAL, "unknown engine");
     if (p->engine == OF_ENGINE_PLAIN && p->precision != OF_PREC_FP32)
         return fail(OF_EINVAL, "the plain engine runs in FP32 only");
     if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
@@ -236,11 +236,23 @@ struct Batch {
     size_t pairs_off[MAX_LEVELS][2] = {}, tiles_off[MAX_LEVELS] = {}, scal_off[MAX_LEVELS] = {};
     int ntiles[MAX_LEVELS] = {}, tile_h[MAX_LEVELS] = {};
     Geom gmax[MAX_LEVELS] = {};
+    // level-resident pairs per level: flags, count, device list offset, shared memory per CTA
+    std::vector<char> res[MAX_LEVELS];
+    int nres[MAX_LEVELS] = {};
+    size_t reslist_off[MAX_LEVELS] = {}, res_smem[MAX_LEVELS] = {};
     size_t partials = 0, table_off = 0, table_bytes = 0, total = 0;
     std::string key;
 };
 
 Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
+
+// Whether a level of geometry g runs its inner iterations on the level-resident engine: an ADMM
+// method, the level fits one cluster's shared memory and, with the default engine, the level is
+// small enough for the resident launch to beat one streaming kernel per iteration.
+bool use_resident(const of_params *p, Geom g) {
+    if (p->method == OF_PDR || !admm_resident_fits(g)) return false;
+    return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g));
+}
 
 Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
     Batch B;
@@ -268,11 +280,23 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
         for (int l = 0; l < B.L; ++l) {
             long strip_rows = 0;
             Geom gm{0, 0, 0};
+            // the level-resident engine takes this level's eligible pairs only when all their
+            // clusters run at once; otherwise one work-list launch per iteration serves them better
+            B.res[l].assign(n, 0);
+            int elig = 0;
+            for (int k = 0; k < n; ++k) elig += use_resident(p, geom_of(B.pl[k], l)) ? 1 : 0;
+            const bool take = elig > 0 && elig <= admm_resident_max_clusters();
             for (int k = 0; k < n; ++k) {
                 const Geom g = geom_of(B.pl[k], l);
-                strip_rows += (long)((g.W + SWD - 1) / SWD) * g.H;
                 if (g.H > gm.H) gm.H = g.H;
                 if (g.W > gm.W) gm.W = g.W;
+                if (take && use_resident(p, g)) {
+                    B.res[l][k] = 1;
+                    ++B.nres[l];
+                    B.res_smem[l] = std::max(B.res_smem[l], admm_resident_smem(g));
+                    continue;
+                }
+                strip_rows += (long)((g.W + SWD - 1) / SWD) * g.H;
             }
             gm.pitch = pitch_of(gm.W);
             B.gmax[l] = gm;
@@ -280,6 +304,7 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             const int rows = B.tile_h[l] * NWP;
             int nt = 0;
             for (int k = 0; k < n; ++k) {
+                if (B.res[l][k]) continue;
                 const Geom g = geom_of(B.pl[k], l);
                 nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
             }
@@ -292,6 +317,8 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             t += align_up(sizeof(TileRef) * nt, 256);
             B.scal_off[l] = t;
             t += align_up(sizeof(PairScalars) * n, 256);
+            B.reslist_off[l] = t;
+            t += align_up(sizeof(int) * n, 256);
             const size_t np = std::max((size_t)nt, (size_t)n * pdr_plain_blocks(gm));
             maxpart = std::max(maxpart, np);
         }
@@ -315,7 +342,8 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
         PairIter *pi1 = (PairIter *)(img.data() + B.pairs_off[l][1]);
         TileRef *tr = (TileRef *)(img.data() + B.tiles_off[l]);
         PairScalars *ps = (PairScalars *)(img.data() + B.scal_off[l]);
-        int t = 0;
+        int *rl = (int *)(img.data() + B.reslist_off[l]);
+        int t = 0, r = 0;
         const int G = pdr_plain_blocks(B.gmax[l]);
         for (int k = 0; k < B.n; ++k) {
             const Plan &pl = B.pl[k];
@@ -344,8 +372,10 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
             }
             const int rows = B.tile_h[l] * admm_fused_warps(), SWD = admm_fused_strip_w();
             const int t0 = t;
-            for (int ty = 0; ty < (g.H + rows - 1) / rows; ++ty)
-                for (int tx = 0; tx < (g.W + SWD - 1) / SWD; ++tx) tr[t++] = TileRef{k, tx, ty, 0};
+            if (B.res[l][k]) rl[r++] = k;
+            else
+                for (int ty = 0; ty < (g.H + rows - 1) / rows; ++ty)
+                    for (int tx = 0; tx < (g.W + SWD - 1) / SWD; ++tx) tr[t++] = TileRef{k, tx, ty, 0};
             ps[k].res_check = &misc->res_check;
             ps[k].res_final = &misc->res_final;
             ps[k].done = &misc->done;
@@ -353,6 +383,7 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
             ps[k].rows = (double)g.H * g.W * (p->beta != 0.f ? 3.0 : 2.0);
             ps[k].part_begin = pdr ? k * G : t0;
             ps[k].part_end = pdr ? (k + 1) * G : t;
+            ps[k].resident = B.res[l][k];
         }
     }
     OF_CUDA(cudaMemcpy(ctx->arena + B.table_off, img.data(), img.size(), cudaMemcpyHostToDevice));
@@ -467,7 +498,46 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 pflow = PREC_F32;
             }
             const int start = cur;
-            for (int it = 0; it < p->iters; ++it) {
+            // level-resident engine: the single pair, or the batch's resident pairs, in one launch
+            const bool res1 = !batched && use_resident(p, geom_of(*pc[0].pl, l));
+            const bool resb = batched && B.nres[l] > 0;
+            if (p->iters > 0 && (res1 || resb)) {
+                ResArgs r{};
+                r.k = k;
+                r.iters = p->iters;
+                r.check = p->tol > 0.0;
+                r.final_res = last_warp;
+                r.tol = p->tol;
+                r.parity_in = start;
+                r.parity_out = (start + p->iters) & 1;
+                if (res1) {
+                    const PairCtx &c = pc[0];
+                    const Geom g = geom_of(*c.pl, l);
+                    const Fields *bf = bufs_of(c);
+                    const void *const *dat = data_of(c);
+                    r.g = g;
+                    r.in = bf[r.parity_in];
+                    r.out = bf[r.parity_out];
+                    r.Ix = dat[0];
+                    r.Iy = dat[1];
+                    r.It = dat[2];
+                    r.ms_max = &c.misc->ms_max;
+                    r.sc.res_check = &c.misc->res_check;
+                    r.sc.res_final = &c.misc->res_final;
+                    r.sc.done = &c.misc->done;
+                    r.sc.iters = &c.misc->iters;
+                    r.sc.rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
+                    r.sc.resident = 1;
+                    launch_admm_resident(r, 1, admm_resident_smem(g), prec, pflow, s);
+                } else {
+                    r.pairs = (const PairIter *)(ctx->arena + B.table_off + B.pairs_off[l][in32 ? 1 : 0]);
+                    r.scal = (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]);
+                    r.list = (const int *)(ctx->arena + B.table_off + B.reslist_off[l]);
+                    launch_admm_resident(r, B.nres[l], B.res_smem[l], prec, pflow, s);
+                }
+            }
+            const bool streamed = batched ? B.ntiles[l] > 0 || pdr : !res1;
+            for (int it = 0; streamed && it < p->iters; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it == p->iters - 1;
                 IterArgs a{};
@@ -523,7 +593,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             const PairScalars *ps = batched ? (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]) : nullptr;
             if (batched) {
                 launch_count_iters_batched(ps, n, p->tol > 0.0 ? p->iters % 10 : p->iters, p->tol > 0.0, s);
-            } else {
+            } else if (!res1) {
                 Misc *m = pc[0].misc;
                 if (p->tol > 0.0) launch_count_iters(&m->iters, &m->done, p->iters % 10, s);
                 else launch_count_iters(&m->iters, nullptr, p->iters, s);
@@ -532,11 +602,12 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 const int fin = (start + p->iters) & 1;
                 if (p->tol > 0.0 && (p->iters & 1))
                     for (int q = 0; q < n; ++q)
-                        launch_parity_fix(bufs_of(pc[q])[start], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l), prec,
+                        if (!(res1 || (batched && B.res[l][q])))  // the resident engine writes buf[fin] itself
+                            launch_parity_fix(bufs_of(pc[q])[start], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l), prec,
                                           pflow, &pc[q].misc->done, 1, s);
                 cur = fin;
             }
-            if (last_warp && p->iters > 0) {
+            if (last_warp && p->iters > 0 && !res1) {
                 if (batched) {
                     launch_reduce_check_batched(bpart, ps, n, 0.0, 0, 1, s);
                 } else {
@@ -649,6 +720,7 @@ of_status of_create(of_ctx **out, int device, size_t hbm_budget_bytes) {
     OF_CUDA(cudaGetDeviceCount(&n));
     if (device < 0 || device >= n) return fail(OF_EINVAL, "no such CUDA device");
     OF_CUDA(cudaSetDevice(device));
+    admm_resident_max_clusters();  // device queries run once, outside any stream capture
     of_ctx *ctx = new of_ctx();
     ctx->device = device;
     size_t fr = 0, tot = 0;

@@ -21,6 +21,13 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// x rounded to storage type T and back: the value a store of x followed by a load yields.
+template <typename T> __device__ __forceinline__ float storage_round(float x) {
+    T t;
+    Store<T>::st(&t, x);
+    return Store<T>::ld(&t);
+}
+
 template <typename T> __device__ __forceinline__ float ldT(const void *base, size_t off) {
     return Store<T>::ld(reinterpret_cast<const T *>(base) + off);
 }

@@ -54,6 +54,7 @@ struct PairScalars {
     long long *iters;
     int part_begin, part_end;
     double rows;
+    int resident, pad_;  // resident: this pair's level runs on the level-resident engine
 };
 
 // One work-list entry of a batched launch: pair index, tile column, tile row.
@@ -80,13 +81,42 @@ struct IterArgs {
 };
 
 // Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w() output
-// columns and TY rows (TY = 1, 2, 8 or 32, chosen per level by admm_fused_tile_h); a block stacks
+// columns and TY rows (TY = 1, 2, 4, 8, 16 or 32, chosen per level by admm_fused_tile_h); a block stacks
 // admm_fused_warps() strips vertically.  A work-list entry (pair, tx, ty) is the block covering
 // columns [tx * strip_w, ...) and rows [ty * warps * TY, ...).
 int admm_fused_tile_h(Geom g);
 int admm_fused_rows_per_warp(long strip_rows);   // strip_rows: sum over pairs of strips x rows
 int admm_fused_strip_w();
 int admm_fused_warps();
+
+// Level-resident fused ADMM engine (k_admm_resident.cu): one thread-block cluster per pair keeps
+// a whole level in shared memory and runs all inner iterations of one warp in one launch, with
+// the stopping test, the iteration count, res_check / res_final and the done flag handled inside
+// (the scalars of PairScalars).  Reads the state from `in` (buf[parity_in]) and writes the final
+// state to `out` (buf[parity_out]); in may equal out.
+struct ResArgs {
+    Coefs k{};
+    // single pair (pairs == nullptr)
+    Geom g{};
+    Fields in{}, out{};
+    const void *Ix = nullptr, *Iy = nullptr, *It = nullptr;
+    const float *ms_max = nullptr;
+    PairScalars sc{};
+    // batched: cluster c works on pair list[c] of pairs[] with the scalars scal[list[c]]
+    const PairIter *pairs = nullptr;
+    const PairScalars *scal = nullptr;
+    const int *list = nullptr;
+    int parity_in = 0, parity_out = 0;
+    int iters = 0, check = 0, final_res = 0;
+    double tol = 0.0;
+};
+int admm_resident_cluster();           // CTAs per cluster: 16 where the device schedules it, else 8
+int admm_resident_max_clusters();      // resident clusters that run at once (one CTA per SM)
+size_t admm_resident_smem(Geom g);     // dynamic shared memory of one CTA for this level
+bool admm_resident_fits(Geom g);       // whether a level of this geometry fits one cluster
+bool admm_resident_preferred(Geom g);  // whether the resident launch is the faster engine for it
+cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, size_t smem, int prec, int prec_flow,
+                                 cudaStream_t s);
 
 // ---------------------------------------------------------------- pyramid / warp (k_pyramid.cu)
 constexpr int MAX_GAUSS_R = 16;

@@ -18,7 +18,7 @@ _lib = None
 OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_ETIMEOUT, OF_ENUMERIC, OF_EBUSY = range(7)
 OF_PADMM_I, OF_PADMM_II, OF_PDR = 0, 1, 2
 OF_PREC_FP32, OF_PREC_FP16, OF_PREC_BF16 = 0, 1, 2
-OF_ENGINE_FUSED, OF_ENGINE_PLAIN = 0, 1
+OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT = 0, 1, 2, 3
 
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
            "of_solve_kernel_count", "of_solve",
@@ -160,6 +160,14 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def of_solve_kernel_count(ctx: Context, H, W, params: of_params) -> int:
+    """Kernel launches in one solve's graph (captures the graph if needed)."""
+    n = lib().of_solve_kernel_count(ctx.h, int(H), int(W), ctypes.byref(params))
+    if n < 0:
+        raise OfError(OF_EINVAL, lib().of_last_error(ctx.h).decode())
+    return int(n)
 
 
 def of_solve(ctx: Context, I0, I1, params: of_params, want_w=False, stats=True, stream=None):

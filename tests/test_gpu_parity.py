@@ -283,11 +283,14 @@ def _batch_pairs():
 
 @pytest.mark.parametrize("name,prec,tol", [("padmm", 0, 0.0), ("rpadmm2", 0, 0.0), ("zach", 0, 0.0), ("pdr", 0, 0.0),
                                            ("padmm", 2, 0.0), ("pdr", 1, 0.0), ("padmm", 0, 3e-3), ("pdr", 0, 3e-3)])
-def test_batch_equals_single(ctx, name, prec, tol):
-    """Uneven sizes solved in one batch (one work-list launch per iteration) give bitwise the
-    results of the separate single-pair solves."""
+@pytest.mark.parametrize("engine", [flow.OF_ENGINE_FUSED, flow.OF_ENGINE_STREAM])
+def test_batch_equals_single(ctx, name, prec, tol, engine):
+    """Uneven sizes solved in one batch (one work-list launch per iteration, or one level-resident
+    launch per warp) give bitwise the results of the separate single-pair solves."""
+    if name == "pdr" and engine == flow.OF_ENGINE_STREAM:
+        pytest.skip("pDR has one fused engine")
     pairs = _batch_pairs()
-    P = flow.default_params(lam=2.0, precision=prec, tol=tol, iters=40, **METHODS[name])
+    P = flow.default_params(lam=2.0, precision=prec, tol=tol, iters=40, engine=engine, **METHODS[name])
     us, vs, sts = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], P)
     for p, u, v, st in zip(pairs, us, vs, sts):
         su, sv, _, sst = flow.of_solve(ctx, cu(p.I0), cu(p.I1), P)
