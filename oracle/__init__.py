@@ -13,6 +13,8 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   srbgs ................. pinned (red-black GS property, convergence to a direct sparse solve)
   admm_step ............. pinned (subproblem optimality, special cases, strong duality)
   pdr_step .............. pinned (same minimum as ADMM, dual certificate, SRBGS limit)
+  cp_step (ALG1) ........ pinned (dual step = projection, primal step = prox optimality,
+                          same certified minimum as ADMM at a fixed linearisation)
   pyramid / upsample .... pinned only by exactness properties (constants, ramps, ratios)
   warp_linearise ........ pinned by identities (zero flow, integer shifts, rho(d0) = I1w - I0)
   solve (end to end) .... pinned by known-flow recovery; absolute values otherwise
@@ -35,6 +37,7 @@ _lib = None
 METHOD_PADMM_I = 0   # rpADMMI (pADMM when r = 1; Zach-pADMM when beta = 0 and r = 1)
 METHOD_PADMM_II = 1  # rpADMMII
 METHOD_PDR = 2       # pDR with red-black symmetric Gauss-Seidel
+METHOD_CP = 3        # ALG1: the primal-dual method of Chambolle and Pock (Sec. 4)
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +56,8 @@ class _Params(ctypes.Structure):
                 ("r", ctypes.c_double), ("rho", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("tau", ctypes.c_double), ("gs_sweeps", ctypes.c_int), ("eta", ctypes.c_double),
                 ("levels", ctypes.c_int), ("warps", ctypes.c_int), ("iters", ctypes.c_int),
-                ("tol", ctypes.c_double), ("out_level", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_double),
+                ("cp_sigma", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -81,11 +85,13 @@ class Params:
     iters: int = 50
     tol: float = 0.0
     out_level: int = 0
+    cp_tau: float = 0.1      # ALG1 dual step (Sec. 4)
+    cp_sigma: float = 1.25   # ALG1 primal step 1 / (8 cp_tau) (Sec. 4, reading of the step rule)
 
     def _c(self) -> _Params:
         return _Params(self.method, self.lam, self.beta, self.c, self.a, self.a_tilde, self.r,
                        self.rho, self.sigma, self.tau, self.gs_sweeps, self.eta, self.levels,
-                       self.warps, self.iters, self.tol, self.out_level)
+                       self.warps, self.iters, self.tol, self.out_level, self.cp_tau, self.cp_sigma)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -116,6 +122,7 @@ def lib():
             "orc_dual_value": (d, [sz, _D, _D]),
             "orc_admm_step_flat": (d, [i, i, PP, _D, _D, _D, d, ctypes.POINTER(_Params)]),
             "orc_pdr_step_flat": (d, [i, i, PP, _D, _D, _D, ctypes.POINTER(_Params)]),
+            "orc_cp_step_flat": (d, [i, i, PP, _D, _D, _D, ctypes.POINTER(_Params)]),
             "orc_inner_flat": (ctypes.c_longlong, [i, i, PP, _D, _D, _D, d, ctypes.POINTER(_Params), i, _D]),
             "orc_solve": (i, [i, i, _D, _D, ctypes.POINTER(_Params), _D, _D, _D, ctypes.POINTER(_Stats)]),
         }
@@ -284,6 +291,14 @@ def pdr_step(state: State, Ix, Iy, It, params: Params) -> float:
     H, W = dat[0].shape
     P = params._c()
     return lib().orc_pdr_step_flat(H, W, state._ptrs(), *[_p(x) for x in dat], ctypes.byref(P))
+
+
+def cp_step(state: State, Ix, Iy, It, params: Params) -> float:
+    """One ALG1 (primal-dual) iteration in place; returns ||X^{k+1} - X^k||^2."""
+    dat = [_f64(x) for x in (Ix, Iy, It)]
+    H, W = dat[0].shape
+    P = params._c()
+    return lib().orc_cp_step_flat(H, W, state._ptrs(), *[_p(x) for x in dat], ctypes.byref(P))
 
 
 def inner(state: State, Ix, Iy, It, a_tilde, params: Params, iters: int):

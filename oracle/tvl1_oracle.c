@@ -294,7 +294,7 @@ double orc_warp_linearise(int H, int W, const double *I0, const double *I1, cons
 /* ------------------------------------------------------------------------------------- */
 
 typedef struct {
-    int method;        /* 0 = rpADMMI (pADMM if r = 1), 1 = rpADMMII, 2 = pDR */
+    int method;        /* 0 = rpADMMI (pADMM if r = 1), 1 = rpADMMII, 2 = pDR, 3 = ALG1 (primal-dual) */
     double lambda;     /* data weight, |s| <= lambda */
     double beta;       /* illumination weight; 0 = the beta = 0 model (no w, no p) */
     double c;          /* ADMM penalty c */
@@ -308,11 +308,14 @@ typedef struct {
     int levels, warps, iters;
     double tol;        /* > 0: stop a warp's inner loop once the residual < tol (checked every 10) */
     int out_level;     /* stop after this pyramid level and return its flow */
+    double cp_tau;     /* ALG1 dual step */
+    double cp_sigma;   /* ALG1 primal step */
 } orc_params;
 
 typedef struct {
     /* ADMM: Lagrange multipliers (w, u, v), duals p, q, s.
-     * pDR: X = (w, u, v), Xbar = (wb, ub, vb), ybar = (p, q); s unused. */
+     * pDR: X = (w, u, v), Xbar = (wb, ub, vb), ybar = (p, q); s unused.
+     * ALG1: X = (w, u, v), the extrapolated Xbar = (wb, ub, vb), y = (p, q); s unused. */
     double *w, *u, *v;
     double *p1, *p2, *q11, *q12, *q21, *q22, *s;
     double *wb, *ub, *vb;
@@ -513,6 +516,75 @@ double orc_pdr_step(int H, int W, orc_state *st, const double *Ix, const double 
 }
 
 /* ------------------------------------------------------------------------------------- */
+/* ALG1 (Sec. 4): the first-order primal-dual method of Chambolle and Pock with constant   */
+/* steps and theta = 1, applied to the saddle-point form eq. (primal-dual:optical:o) with   */
+/* K = (grad w, grad u, grad v), F(X) = lambda ||rho(w, d)||_1, G^* = the indicators of     */
+/* the unit balls of p and (jointly) q.  One iteration:                                     */
+/*   y^{k+1}    = P(y^k + tau K Xbar^k)              (P_p on p, P_q on q)                    */
+/*   X^{k+1}    = prox_{sigma F}(X^k - sigma K^* y^{k+1}) = prox_{sigma F}(X^k + sigma div y) */
+/*   Xbar^{k+1} = 2 X^{k+1} - X^k.                                                           */
+/* Reading: the printed step rule "sigma = 1/(L^2 sigma)" is sigma = 1/(L^2 tau), L^2 = 8,   */
+/* with tau = 0.1 the dual step, so sigma = 1.25.  Returns ||X^{k+1} - X^k||^2.              */
+/* ------------------------------------------------------------------------------------- */
+
+double orc_cp_step(int H, int W, orc_state *st, const double *Ix, const double *Iy,
+                   const double *It, const orc_params *P)
+{
+    size_t N = (size_t)H * (size_t)W;
+    int has_w = P->beta != 0.0;
+    double ta = P->cp_tau, sg = P->cp_sigma;
+    double *gx = orc_alloc(N), *gy = orc_alloc(N), *gx2 = orc_alloc(N), *gy2 = orc_alloc(N);
+    double *d = orc_alloc(N), *zw = orc_alloc(N), *zu = orc_alloc(N), *zv = orc_alloc(N);
+    double diff2 = 0.0;
+
+    /* dual ascent on the extrapolated primal point, then projection */
+    if (has_w) {
+        orc_grad(H, W, st->wb, gx, gy);
+        for (size_t k = 0; k < N; ++k) { st->p1[k] += ta * gx[k]; st->p2[k] += ta * gy[k]; }
+        orc_proj_p(N, st->p1, st->p2);
+    }
+    orc_grad(H, W, st->ub, gx, gy);
+    orc_grad(H, W, st->vb, gx2, gy2);
+    for (size_t k = 0; k < N; ++k) {
+        st->q11[k] += ta * gx[k];
+        st->q12[k] += ta * gy[k];
+        st->q21[k] += ta * gx2[k];
+        st->q22[k] += ta * gy2[k];
+    }
+    orc_proj_q(N, st->q11, st->q12, st->q21, st->q22);
+    /* primal descent along div y^{k+1}, then the L1 resolvent */
+    if (has_w) {
+        orc_div(H, W, st->p1, st->p2, d);
+        for (size_t k = 0; k < N; ++k) zw[k] = st->w[k] + sg * d[k];
+    }
+    orc_div(H, W, st->q11, st->q12, d);
+    for (size_t k = 0; k < N; ++k) zu[k] = st->u[k] + sg * d[k];
+    orc_div(H, W, st->q21, st->q22, d);
+    for (size_t k = 0; k < N; ++k) zv[k] = st->v[k] + sg * d[k];
+    orc_prox_l1(N, zw, zu, zv, Ix, Iy, It, P->beta, P->lambda, sg);
+    /* extrapolation */
+    for (size_t k = 0; k < N; ++k) {
+        double e;
+        if (has_w) {
+            e = zw[k] - st->w[k];
+            diff2 += e * e;
+            st->wb[k] = 2.0 * zw[k] - st->w[k];
+            st->w[k] = zw[k];
+        }
+        e = zu[k] - st->u[k];
+        diff2 += e * e;
+        st->ub[k] = 2.0 * zu[k] - st->u[k];
+        st->u[k] = zu[k];
+        e = zv[k] - st->v[k];
+        diff2 += e * e;
+        st->vb[k] = 2.0 * zv[k] - st->v[k];
+        st->v[k] = zv[k];
+    }
+    free(gx); free(gy); free(gx2); free(gy2); free(d); free(zw); free(zu); free(zv);
+    return diff2;
+}
+
+/* ------------------------------------------------------------------------------------- */
 /* Energy of the discrete primal problem, eq. (l1:finite): ||grad w||_1 + ||grad d||_1     */
 /* + lambda ||rho(w, d)||_1, with the pointwise norms of eq. (euclid:norm) (joint for d),  */
 /* and the dual objective <It, s> of eq. (dual:l1:flow:cons).                              */
@@ -557,8 +629,9 @@ long long orc_inner(int H, int W, orc_state *st, const double *Ix, const double 
     double res = 0.0;
     long long k;
     for (k = 0; k < iters; ++k) {
-        double r2 = (P->method == 2) ? orc_pdr_step(H, W, st, Ix, Iy, It, P)
-                                     : orc_admm_step(H, W, st, Ix, Iy, It, a_tilde, P);
+        double r2 = P->method == 2   ? orc_pdr_step(H, W, st, Ix, Iy, It, P)
+                     : P->method == 3 ? orc_cp_step(H, W, st, Ix, Iy, It, P)
+                                      : orc_admm_step(H, W, st, Ix, Iy, It, a_tilde, P);
         res = sqrt(r2 / nrows);
         if (P->tol > 0.0 && (k + 1) % 10 == 0 && res < P->tol) { ++k; break; }
     }
@@ -617,7 +690,7 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
             for (int f = 3; f < 13; ++f) memset(*fields[f], 0, n * sizeof(double));
         }
         if (P->beta == 0.0) memset(st.w, 0, n * sizeof(double));
-        if (P->method == 2) {
+        if (P->method == 2 || P->method == 3) { /* pDR: Xbar = X; ALG1: the extrapolated point starts at X */
             memcpy(st.wb, st.w, n * sizeof(double)); memcpy(st.ub, st.u, n * sizeof(double)); memcpy(st.vb, st.v, n * sizeof(double));
         }
         orc_derivatives(h, w, P1[l], I1x, I1y);
@@ -636,7 +709,7 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
                 stats->iters_run = total;
                 stats->residual = res;
                 stats->energy = orc_energy(h, w, st.w, st.u, st.v, Ix, Iy, It, P->beta, P->lambda);
-                stats->dual_value = P->method == 2 ? NAN : orc_dual_value(n, It, st.s);
+                stats->dual_value = P->method >= 2 ? NAN : orc_dual_value(n, It, st.s);
             }
         }
     }
@@ -667,6 +740,14 @@ double orc_pdr_step_flat(int H, int W, double **fields, const double *Ix, const 
     orc_state st;
     orc_state_from(&st, fields);
     return orc_pdr_step(H, W, &st, Ix, Iy, It, P);
+}
+
+double orc_cp_step_flat(int H, int W, double **fields, const double *Ix, const double *Iy,
+                        const double *It, const orc_params *P)
+{
+    orc_state st;
+    orc_state_from(&st, fields);
+    return orc_cp_step(H, W, &st, Ix, Iy, It, P);
 }
 
 long long orc_inner_flat(int H, int W, double **fields, const double *Ix, const double *Iy,

@@ -92,7 +92,7 @@ def test_warp_identities(orc):
     np.testing.assert_allclose(It[inner], 0.0, atol=1e-14)
 
 
-@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("method", [0, 1, 2, 3])
 def test_known_flow_recovery(orc, method):
     """64 x 48 sinusoid pair with a piecewise-constant motion: with a data weight that lets the
     data term speak (lambda = 5 on [0, 1] intensities) every solver recovers the motion.

@@ -1,6 +1,7 @@
 """Pins of the oracle's solver iterations: red-black SGS (Sec. 3.1.2), the rpADMMI / rpADMMII /
-Zach-pADMM updates (Sec. 3.1.1, appendix derivation of the y/s updates), pDR (Sec. 3.1.2) and
-their common fixed point (Props. 3.1 and 3.2, strong duality of Sec. 2.2).
+Zach-pADMM updates (Sec. 3.1.1, appendix derivation of the y/s updates), pDR (Sec. 3.1.2), the
+ALG1 primal-dual comparison solver (Sec. 4) and their common fixed point (Props. 3.1 and 3.2,
+strong duality of Sec. 2.2).
 
 The sparse operators come from tests/_mats.py, built entry by entry from the definitions, so
 these checks share nothing with the oracle's C code."""
@@ -265,6 +266,59 @@ def test_pdr_step_matches_generic_form_with_exact_inner_solve(orc):
                                _ball(qo + 2 * P.tau * gq) - P.tau * gq, atol=1e-12)
 
 
+@pytest.mark.parametrize("beta", [0.05, 0.0])
+def test_alg1_step_is_dual_projection_then_primal_prox(orc, beta):
+    """ALG1 (Chambolle-Pock, theta = 1): y' is the projection of y + tau K Xbar (P_p, joint P_q);
+    X' minimises sigma lambda |rho(X)| + |X - Z|^2 / 2 pointwise with Z = X - sigma K^* y'
+    (checked against the objective at perturbed points and by a 1-D search along e);
+    Xbar' = 2 X' - X."""
+    H, W = 6, 7
+    rng, d, _, lam = _random_problem(H, W, 31, beta=beta)
+    P = orc.Params(method=3, lam=lam, beta=beta, cp_tau=0.1, cp_sigma=1.25)
+    st = _random_state(orc, rng, H, W, lam, beta)
+    for k in ("wb", "ub", "vb"):
+        st[k] = rng.normal(size=(H, W)) if (beta != 0.0 or k != "wb") else np.zeros((H, W))
+    old = st.copy()
+    r2 = orc.cp_step(st, d["Ix"], d["Iy"], d["It"], P)
+    ops = _Ops(H, W)
+    # dual step
+    if beta != 0.0:
+        np.testing.assert_allclose(_flat(st, "p1", "p2"), _ball(_flat(old, "p1", "p2") + P.cp_tau * ops.grad(old["wb"])),
+                                   atol=1e-13)
+    qn = _ball(np.vstack([_flat(old, "q11", "q12") + P.cp_tau * ops.grad(old["ub"]),
+                          _flat(old, "q21", "q22") + P.cp_tau * ops.grad(old["vb"])]))
+    np.testing.assert_allclose(np.vstack([_flat(st, "q11", "q12"), _flat(st, "q21", "q22")]), qn, atol=1e-13)
+    # primal step: pointwise minimiser of sigma lambda |rho(X)| + |X - Z|^2 / 2
+    Z = [old[x].ravel() - P.cp_sigma * ops.Bt(_flat(st, *c)) for x, c in
+         (("w", ("p1", "p2")), ("u", ("q11", "q12")), ("v", ("q21", "q22")))]
+    if beta == 0.0:
+        Z[0] = np.zeros(H * W)
+    Xn = np.stack([st[x].ravel() for x in ("w", "u", "v")])
+    Z = np.stack(Z)
+    e = np.stack([np.full(H * W, beta), d["Ix"].ravel(), d["Iy"].ravel()])
+    It = d["It"].ravel()
+
+    def obj(X):
+        return P.cp_sigma * lam * np.abs(It + np.sum(e * X, 0)) + 0.5 * np.sum((X - Z) ** 2, 0)
+
+    f0 = obj(Xn)
+    for _ in range(40):
+        dX = rng.normal(size=Xn.shape) * 10.0 ** rng.uniform(-6, -1)
+        if beta == 0.0:
+            dX[0] = 0.0
+        assert np.all(obj(Xn + dX) >= f0 - 1e-12)
+    # the minimiser lies on the line Z + t e: no point of it does better
+    ts = np.linspace(-3.0, 3.0, 6001)
+    for k in range(H * W):
+        ek = e[:, k]
+        line = P.cp_sigma * lam * np.abs(It[k] + ek @ Z[:, k] + ts * (ek @ ek)) + 0.5 * ts ** 2 * (ek @ ek)
+        assert f0[k] <= line.min() + 1e-12
+    # extrapolation and the returned step size
+    for x, xb in (("w", "wb"), ("u", "ub"), ("v", "vb")):
+        np.testing.assert_allclose(st[xb], 2 * st[x] - old[x], atol=1e-13)
+    assert r2 == pytest.approx(sum(np.sum((st[x] - old[x]) ** 2) for x in ("w", "u", "v")), rel=1e-12)
+
+
 # ------------------------------------------------------------------------ fixed point
 def _primal_energy_dense(H, W, X, d, beta, lam):
     ops = _Ops(H, W)
@@ -341,6 +395,12 @@ def test_solvers_reach_the_same_minimum_with_a_dual_certificate(orc):
     ref = energies["padmm"]
     for k, e in energies.items():
         assert abs(e - ref) < 1e-6 * ref, (k, energies)
+    # ALG1 (constant steps tau = 0.1, sigma = 1.25) reaches the certified minimum as well
+    P = orc.Params(method=3, lam=lam, beta=beta, cp_tau=0.1, cp_sigma=1.25)
+    st = orc.State.zeros(H, W)
+    orc.inner(st, d["Ix"], d["Iy"], d["It"], at, P, 200000)
+    ecp = orc.energy(st["w"], st["u"], st["v"], d["Ix"], d["Iy"], d["It"], beta, lam)
+    assert abs(ecp - ref) < 1e-7 * ref, (ecp, ref)
     # The dense generic solve converges slowly (O(1/k)); it must never find a lower energy than
     # the certified minimum and must approach it.
     Xbf = _pdhg_bruteforce(H, W, d, beta, lam)
@@ -353,6 +413,6 @@ def test_zero_motion_pair_stays_zero(orc):
     """I1 = I0: at zero flow It = 0, every update keeps the whole state at exactly zero."""
     from paper_2011_10979_gb300 import synth
     pr = synth.sinusoid_pair(seed=5)
-    for m in (0, 1, 2):
+    for m in (0, 1, 2, 3):
         u, v, w, st = orc.solve(pr.I0, pr.I0, orc.Params(method=m, levels=2, warps=2, iters=20))
         assert np.all(u == 0.0) and np.all(v == 0.0) and np.all(w == 0.0)
