@@ -229,6 +229,7 @@ def run_ours(args):
     batch = batch_measure(flow, torch, dev, fp32_flow=1)
     batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
     prec_line = precision_measure(flow, torch, dev)
+    solvers = solvers_measure(flow, torch, dev, I0, I1, pr)
     if rank != 0:
         return
     cpu = None
@@ -258,6 +259,7 @@ def run_ours(args):
             "serving": serving,
             "batch_all16": batch_all16,
             "precision_1024x436": prec_line,
+            "solvers_640x480": solvers,
             "cpu_baseline": cpu,
             "e2e": {"value": whole_job_rate(1, ws, t_e2e), "unit": "flows/s", "h2d_bytes_per_step": 2 * H * W * 4,
                     "d2h_bytes_per_step": 2 * H * W * 4},
@@ -340,6 +342,38 @@ def precision_measure(flow, torch, dev):
     return out
 
 
+def solvers_measure(flow, torch, dev, I0, I1, pr):
+    """Every solver of the library on the bench workload (640 x 480, 5 levels x 10 warps x 100
+    iterations, FP32, default engines), as the paper's Sec. 4 compares them: device time per
+    solve and the end-point error against the pair's known motion (where it is defined)."""
+    ctx = flow.Context(dev.index or 0)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, kw in (("pADMM", dict(method=flow.OF_PADMM_I, r=1.0)), ("rpADMMI", dict(method=flow.OF_PADMM_I, r=1.618)),
+                     ("rpADMMII", dict(method=flow.OF_PADMM_II, rho=1.9)),
+                     ("Zach-pADMM", dict(method=flow.OF_PADMM_I, r=1.0, beta=0.0)),
+                     ("pDR", dict(method=flow.OF_PDR)), ("ALG1", dict(method=flow.OF_CP))):
+        kw = dict(dict(lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS), **kw)
+        P = flow.default_params(**kw)
+        u, v, _, _ = flow.of_solve(ctx, I0, I1, P, stats=False)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            u, v, _, _ = flow.of_solve(ctx, I0, I1, P, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 3
+        r = {"ms_per_solve": ms, "flows_per_s": 1e3 / ms, "launches": flow.of_solve_kernel_count(ctx, H, W, P)}
+        if pr.u_true is not None:
+            ut = torch.from_numpy(pr.u_true.astype(np.float32)).to(dev)
+            vt = torch.from_numpy(pr.v_true.astype(np.float32)).to(dev)
+            r["epe_vs_true_px"] = float(torch.hypot(u - ut, v - vt).mean())
+        out[name] = r
+    ctx.close()
+    return out
+
+
 def serving_measure(flow, torch, dev, rate_hz=20.0, duration_s=10.0, max_active=8):
     """Serving loop under Poisson arrivals (rate_hz for duration_s), request sizes drawn from
     {320x240: 40%, 640x480: 30%, 1024x436: 20%, 1920x1080: 8%, 3840x2160: 2%} with layered motion
@@ -391,8 +425,9 @@ def serving_measure(flow, torch, dev, rate_hz=20.0, duration_s=10.0, max_active=
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streaming pADMM kernel on the
-# 640 x 480 level (ncu, cold cache).  None until the current kernel has been captured.
-ROLL_640_DRAM_BYTES = None
+# 640 x 480 level (ncu, cold cache): 16.07 MB read + 4 KB written (the written planes stay in L2).
+# Set to None whenever that kernel changes, until it is captured again.
+ROLL_640_DRAM_BYTES = 16.07e6
 
 
 def kernel_roofline(flow, torch, dev, pr, reps=20):

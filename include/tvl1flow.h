@@ -48,7 +48,9 @@ typedef enum {
 typedef enum {
     OF_PADMM_I = 0,   /* rpADMMI, Sec. 3.1.1 eq. (rpADMMI); r = 1 is pADMM; beta = 0 is Zach-pADMM */
     OF_PADMM_II = 1,  /* rpADMMII, Sec. 3.1.1 eq. (rpADMMII) */
-    OF_PDR = 2        /* pDR, Sec. 3.1.2 eq. (pDR) with SRBGS preconditioner */
+    OF_PDR = 2,       /* pDR, Sec. 3.1.2 eq. (pDR) with SRBGS preconditioner */
+    OF_CP = 3         /* ALG1, the comparison solver of Sec. 4: the primal-dual method of
+                         Chambolle and Pock with constant steps cp_tau (dual), cp_sigma (primal) */
 } of_method;
 
 typedef enum { OF_PREC_FP32 = 0, OF_PREC_FP16 = 1, OF_PREC_BF16 = 2 } of_precision;
@@ -89,14 +91,16 @@ typedef struct {
                             dual fields and the linearisation data in 16 bits               */
     int engine;          /* of_engine                                                           */
     int out_level;       /* stop after this pyramid level and return its flow (0 = finest)     */
+    float cp_tau;        /* ALG1 dual step (Sec. 4: 0.1)                                        */
+    float cp_sigma;      /* ALG1 primal step; Sec. 4's garbled rule read as 1 / (8 cp_tau) = 1.25 */
 } of_params;
 
 typedef struct {
     long long iters_run; /* inner iterations executed over the whole schedule                   */
     double residual;     /* last residual: ||A s + B y|| / sqrt(rows) (ADMM) or
-                            ||X^{k+1} - X^k|| / sqrt(rows) (pDR), on the output level          */
+                            ||X^{k+1} - X^k|| / sqrt(rows) (pDR, ALG1), on the output level    */
     double energy;       /* primal energy eq. (l1:finite) at the output level's last linearisation */
-    double dual_value;   /* <It, s> (eq. dual:l1:flow:cons); NaN for pDR                        */
+    double dual_value;   /* <It, s> (eq. dual:l1:flow:cons); NaN for pDR and ALG1               */
     float ms;            /* device time of the solve in milliseconds                            */
 } of_stats;
 
@@ -220,7 +224,15 @@ of_status of_pdr_iterate(of_fields f, const float *Ix, const float *Iy, const fl
                          int W, int pitch, const of_params *params, int iters, void *scratch,
                          double *res2, void *stream);
 
-/* Scratch bytes the fused engine of the two calls above needs for an H-row plane set. */
+/* `iters` ALG1 iterations (Sec. 4; params->method OF_CP) in place on `f`: w u v hold X, wb ub
+ * vb the extrapolated point Xbar, p and q the dual y (s unused).  res2: optional host pointer
+ * receiving ||X^{k+1} - X^k||^2 of the last iteration.  scratch as for of_admm_iterate (the
+ * kernel reads one plane set and writes the other). */
+of_status of_cp_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H,
+                        int W, int pitch, const of_params *params, int iters, void *scratch,
+                        double *res2, void *stream);
+
+/* Scratch bytes the fused engines of the calls above need for an H-row plane set. */
 size_t of_fields_bytes(int H, int pitch);
 
 /* Primal energy eq. (l1:finite) and dual value <It, s> (eq. dual:l1:flow:cons) of FP32 fields,

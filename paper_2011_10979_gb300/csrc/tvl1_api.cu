@@ -68,10 +68,14 @@ struct Misc {
 of_status validate(const of_params *p, int H, int W) {
     if (!p) return fail(OF_EINVAL, "params is NULL");
     if (H < 1 || W < 1) return fail(OF_EINVAL, "image sizes must be >= 1");
-    if (p->method < 0 || p->method > 2) return fail(OF_EINVAL, "unknown method");
+    if (p->method < 0 || p->method > 3) return fail(OF_EINVAL, "unknown method");
     if (!(p->lambda > 0.f) || !isfinite(p->lambda)) return fail(OF_EINVAL, "lambda must be > 0");
     if (!(p->beta >= 0.f) || !isfinite(p->beta)) return fail(OF_EINVAL, "beta must be >= 0");
-    if (p->method != OF_PDR) {
+    if (p->method == OF_CP) {
+        if (!(p->cp_tau > 0.f) || !(p->cp_sigma > 0.f) || !isfinite(p->cp_tau) || !isfinite(p->cp_sigma))
+            return fail(OF_EINVAL, "cp_tau and cp_sigma must be > 0");
+        if (p->engine == OF_ENGINE_PLAIN) return fail(OF_EINVAL, "ALG1 has one (fused) engine");
+    } else if (p->method != OF_PDR) {
         if (!(p->c > 0.f) || !isfinite(p->c)) return fail(OF_EINVAL, "c must be > 0");
         if (!(p->a > 0.f) || !isfinite(p->a)) return fail(OF_EINVAL, "a must be > 0");
         if (!isfinite(p->a_tilde)) return fail(OF_EINVAL, "a_tilde must be finite");
@@ -140,11 +144,14 @@ Plan make_plan(int H, int W, const of_params *p) {
         pl.stA32 = pl.stB32 = pl.data32 = 0;
     }
     pl.tmp = take(6 * pl.plane32);
-    Geom g0{pl.H[0], pl.W[0], pl.P[0]};
-    int mb = admm_fused_blocks(g0);
-    mb = mb > admm_plain_blocks(g0) ? mb : admm_plain_blocks(g0);
-    mb = mb > pdr_plain_blocks(g0) ? mb : pdr_plain_blocks(g0);
-    mb = mb > energy_blocks(g0) ? mb : energy_blocks(g0);
+    // partial-sum slots: the most blocks any engine launches on any level (the streaming engine's
+    // strip height changes with the level, so a coarser level can need more blocks)
+    int mb = 1;
+    for (int l = 0; l < pl.L; ++l) {
+        const Geom g{pl.H[l], pl.W[l], pl.P[l]};
+        mb = std::max({mb, admm_fused_blocks(g), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g),
+                       energy_blocks(g)});
+    }
     pl.max_blocks = mb;
     pl.partials = take(3 * (size_t)mb * sizeof(double));
     pl.misc = take(sizeof(Misc));
@@ -212,6 +219,8 @@ Coefs coefs_of(const of_params *p) {
     k.sigma = p->sigma;
     k.tau = p->tau;
     k.a_tilde_fixed = p->a_tilde;
+    k.cp_tau = p->cp_tau;
+    k.cp_sigma = p->cp_sigma;
     k.method = p->method;
     k.gs_sweeps = p->gs_sweeps;
     return k;
@@ -250,7 +259,7 @@ Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
 // method, the level fits one cluster's shared memory and, with the default engine, the level is
 // small enough for the resident launch to beat one streaming kernel per iteration.
 bool use_resident(const of_params *p, Geom g) {
-    if (p->method == OF_PDR || !admm_resident_fits(g)) return false;
+    if (p->method == OF_PDR || p->method == OF_CP || !admm_resident_fits(g)) return false;
     return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g));
 }
 
@@ -319,7 +328,7 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             t += align_up(sizeof(PairScalars) * n, 256);
             B.reslist_off[l] = t;
             t += align_up(sizeof(int) * n, 256);
-            const size_t np = std::max((size_t)nt, (size_t)n * pdr_plain_blocks(gm));
+            const size_t np = std::max({(size_t)nt, (size_t)n * pdr_plain_blocks(gm), (size_t)n * cp_blocks(gm)});
             maxpart = std::max(maxpart, np);
         }
         B.table_off = off;
@@ -336,7 +345,8 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
 of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
     if (B.n <= 1) return OF_OK;
     std::vector<char> img(B.table_bytes, 0);
-    const bool pdr = p->method == OF_PDR;
+    const bool pdr = p->method == OF_PDR, cp = p->method == OF_CP;
+    const bool xb = pdr || cp;  // one grid slice per pair (pDR, ALG1) instead of a tile work-list
     for (int l = 0; l < B.L; ++l) {
         PairIter *pi0 = (PairIter *)(img.data() + B.pairs_off[l][0]);
         PairIter *pi1 = (PairIter *)(img.data() + B.pairs_off[l][1]);
@@ -344,7 +354,7 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
         PairScalars *ps = (PairScalars *)(img.data() + B.scal_off[l]);
         int *rl = (int *)(img.data() + B.reslist_off[l]);
         int t = 0, r = 0;
-        const int G = pdr_plain_blocks(B.gmax[l]);
+        const int G = cp ? cp_blocks(B.gmax[l]) : pdr_plain_blocks(B.gmax[l]);
         for (int k = 0; k < B.n; ++k) {
             const Plan &pl = B.pl[k];
             char *A = ctx->arena + B.base[k];
@@ -381,8 +391,8 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
             ps[k].done = &misc->done;
             ps[k].iters = &misc->iters;
             ps[k].rows = (double)g.H * g.W * (p->beta != 0.f ? 3.0 : 2.0);
-            ps[k].part_begin = pdr ? k * G : t0;
-            ps[k].part_end = pdr ? (k + 1) * G : t;
+            ps[k].part_begin = xb ? k * G : t0;
+            ps[k].part_end = xb ? (k + 1) * G : t;
             ps[k].resident = B.res[l][k];
         }
     }
@@ -397,10 +407,13 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
     const int n = B.n;
     const bool batched = n > 1;
     const bool has_w = p->beta != 0.f;
-    const bool pdr = p->method == OF_PDR;
+    const bool pdr = p->method == OF_PDR, cp = p->method == OF_CP;
     const bool plain = p->engine == OF_ENGINE_PLAIN;
-    const bool pingpong = !pdr && !plain;
+    const bool pingpong = !pdr && !plain;  // ADMM fused engines and ALG1 read one buffer, write the other
     const GaussTaps taps = gauss_taps(p->eta);
+    auto blocks_of = [&](Geom g) {
+        return pdr ? pdr_plain_blocks(g) : cp ? cp_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
+    };
     const Coefs k = coefs_of(p);
     const int L = B.L;
     double *bpart = batched ? (double *)(ctx->arena + B.partials) : nullptr;
@@ -461,7 +474,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             const int now = l == L - 1 ? cur : cur ^ 1;
             launch_fill(bf[now].f + F_P1, prec, F_S - F_P1 + 1, g, 0.f, s);   // duals p, q, s restart at 0
             if (!has_w) launch_fill(bf[now].f + F_W, pflow, 1, g, 0.f, s);
-            if (pdr) {
+            if (pdr || cp) {  // pDR: Xbar = X; ALG1: the extrapolated point starts at X
                 const void *src[3] = {bf[now].f[F_W], bf[now].f[F_U], bf[now].f[F_V]};
                 void *dst[3] = {bf[now].f[F_WB], bf[now].f[F_UB], bf[now].f[F_VB]};
                 launch_copy_planes(src, dst, 3, g, pflow, s);
@@ -536,7 +549,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     launch_admm_resident(r, B.nres[l], B.res_smem[l], prec, pflow, s);
                 }
             }
-            const bool streamed = batched ? B.ntiles[l] > 0 || pdr : !res1;
+            const bool streamed = batched ? B.ntiles[l] > 0 || pdr || cp : !res1;
             for (int it = 0; streamed && it < p->iters; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it == p->iters - 1;
@@ -560,12 +573,14 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     if (pdr) {
                         if (plain) launch_pdr_plain(a, s);
                         else launch_pdr_fused(a, prec, pflow, s);
+                    } else if (cp) {
+                        launch_cp(a, prec, pflow, s);
                     } else {
                         if (plain) launch_admm_plain(a, s);
                         else launch_admm_fused(a, prec, pflow, s);
                     }
                     if (check) {
-                        const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
+                        const int nb = blocks_of(g);
                         const double rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
                         launch_reduce_check(c.partials, nb, &c.misc->res_check, rows, p->tol, &c.misc->done,
                                             &c.misc->iters, 10, s);
@@ -578,6 +593,11 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         a.ntiles = n;
                         a.parity = start;
                         launch_pdr_fused(a, prec, pflow, s);
+                    } else if (cp) {
+                        a.g = B.gmax[l];
+                        a.ntiles = n;
+                        a.parity = (start + it) & 1;
+                        launch_cp(a, prec, pflow, s);
                     } else {
                         a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
                         a.ntiles = B.ntiles[l];
@@ -612,8 +632,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     launch_reduce_check_batched(bpart, ps, n, 0.0, 0, 1, s);
                 } else {
                     const Geom g = geom_of(*pc[0].pl, l);
-                    const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
-                    launch_sum(pc[0].partials, nb, &pc[0].misc->res_final, s);
+                    launch_sum(pc[0].partials, blocks_of(g), &pc[0].misc->res_final, s);
                 }
             }
         }
@@ -625,7 +644,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 const int mb = pl.max_blocks;
                 double *pe = c.partials + mb, *pd = c.partials + 2 * mb;
                 Fields fe = bufs_of(c)[cur];
-                if (pdr) fe.f[F_S] = nullptr;
+                if (pdr || cp) fe.f[F_S] = nullptr;
                 if (!has_w) fe.f[F_W] = nullptr;
                 const void *const *dat = data_of(c);
                 launch_energy(fe, dat[0], dat[1], dat[2], g, p->beta, p->lambda, prec, pflow, pe, pd, s);
@@ -676,7 +695,7 @@ of_status read_stats(of_ctx *ctx, const Batch &B, int q, const of_params *p, cud
     stats->iters_run = m.iters;
     stats->residual = p->iters > 0 ? sqrt(m.res_final / rows) : 0.0;
     stats->energy = m.energy;
-    stats->dual_value = p->method == OF_PDR ? NAN : m.dual;
+    stats->dual_value = (p->method == OF_PDR || p->method == OF_CP) ? NAN : m.dual;
     if (!isfinite(stats->residual) || !isfinite(stats->energy))
         return fail(OF_ENUMERIC, "non-finite residual or energy (NaN/Inf in the inputs or parameters?)");
     return OF_OK;
@@ -711,6 +730,8 @@ void of_default_params(of_params *p) {
     p->fp32_flow = 1;
     p->engine = OF_ENGINE_FUSED;
     p->out_level = 0;
+    p->cp_tau = 0.1f;
+    p->cp_sigma = 1.25f;
 }
 
 of_status of_create(of_ctx **out, int device, size_t hbm_budget_bytes) {
@@ -936,31 +957,34 @@ size_t of_fields_bytes(int H, int pitch) {
     if (H < 1 || pitch < 1) return 0;
     const size_t plane = align_up((size_t)H * pitch * 4, 256);
     Geom g{H, pitch, pitch};
-    int mb = admm_fused_blocks(g);
-    if (admm_plain_blocks(g) > mb) mb = admm_plain_blocks(g);
-    if (pdr_plain_blocks(g) > mb) mb = pdr_plain_blocks(g);
+    const int mb = std::max({admm_fused_blocks(g), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g)});
     return (NFIELDS + 6) * plane + align_up((size_t)mb * sizeof(double), 256) + align_up(sizeof(Misc), 256);
 }
 
 namespace {
 
+// Step-level iterations of one method family: KIND_ADMM (rpADMMI / rpADMMII), KIND_PDR, KIND_CP.
+enum { KIND_ADMM = 0, KIND_PDR = 1, KIND_CP = 2 };
+
 of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const float *It, int H, int W, int pitch,
                          float a_tilde, const of_params *params, int iters, void *scratch, double *res2, void *stream,
-                         bool pdr) {
+                         int kind) {
     if (!params) return fail(OF_EINVAL, "params is NULL");
     of_status st = validate(params, H, W);
     if (st != OF_OK) return st;
-    if ((params->method == OF_PDR) != pdr) return fail(OF_EINVAL, "params->method does not match the entry point");
+    const int want = params->method == OF_PDR ? KIND_PDR : params->method == OF_CP ? KIND_CP : KIND_ADMM;
+    if (want != kind) return fail(OF_EINVAL, "params->method does not match the entry point");
+    const bool pdr = kind == KIND_PDR, cp = kind == KIND_CP, xb = pdr || cp;
     if (params->precision != OF_PREC_FP32) return fail(OF_EINVAL, "step-level entry points take FP32 fields");
     if (pitch < W || iters < 0) return fail(OF_EINVAL, "bad pitch or iteration count");
-    if (!pdr && !(a_tilde > 0.f)) return fail(OF_EINVAL, "a_tilde must be > 0");
+    if (kind == KIND_ADMM && !(a_tilde > 0.f)) return fail(OF_EINVAL, "a_tilde must be > 0");
     const bool has_w = params->beta != 0.f;
     float *need[] = {f.u, f.v, f.q11, f.q12, f.q21, f.q22};
     for (float *x : need)
         if (!x) return fail(OF_EINVAL, "NULL field pointer");
     if (has_w && (!f.w || !f.p1 || !f.p2)) return fail(OF_EINVAL, "beta > 0 needs w, p1, p2");
-    if (!pdr && !f.s) return fail(OF_EINVAL, "ADMM needs s");
-    if (pdr && (!f.ub || !f.vb || (has_w && !f.wb))) return fail(OF_EINVAL, "pDR needs wb, ub, vb");
+    if (kind == KIND_ADMM && !f.s) return fail(OF_EINVAL, "ADMM needs s");
+    if (xb && (!f.ub || !f.vb || (has_w && !f.wb))) return fail(OF_EINVAL, "pDR and ALG1 need wb, ub, vb");
     if (!Ix || !Iy || !It) return fail(OF_EINVAL, "NULL linearisation data");
     if (!scratch) return fail(OF_EINVAL, "scratch is NULL (size: of_fields_bytes)");
     cudaStream_t s = (cudaStream_t)stream;
@@ -977,9 +1001,7 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
     for (int k = 0; k < NFIELDS; ++k)
         if (!user.f[k]) user.f[k] = other.f[k];
     float *tmp = (float *)(S + NFIELDS * plane);
-    int mb = admm_fused_blocks(g);
-    if (admm_plain_blocks(g) > mb) mb = admm_plain_blocks(g);
-    if (pdr_plain_blocks(g) > mb) mb = pdr_plain_blocks(g);
+    const int mb = std::max({admm_fused_blocks(g), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g)});
     double *partials = (double *)(S + (NFIELDS + 6) * plane);
     Misc *misc = (Misc *)(S + (NFIELDS + 6) * plane + align_up((size_t)mb * sizeof(double), 256));
     OF_CUDA(cudaMemsetAsync(misc, 0, sizeof(Misc), s));
@@ -989,7 +1011,7 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
     const bool pingpong = !pdr && !plain;
     Fields bufs[2] = {user, other};
     of_params pp = *params;
-    pp.a_tilde = pdr ? 1.f : a_tilde;
+    pp.a_tilde = xb ? 1.f : a_tilde;
     const Coefs k = coefs_of(&pp);
     const double rows = (double)H * W * (has_w ? 3.0 : 2.0);
     for (int it = 0; it < iters; ++it) {
@@ -1009,12 +1031,14 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
         if (pdr) {
             if (plain) launch_pdr_plain(a, s);
             else launch_pdr_fused(a, PREC_F32, PREC_F32, s);
+        } else if (cp) {
+            launch_cp(a, PREC_F32, PREC_F32, s);
         } else {
             if (plain) launch_admm_plain(a, s);
             else launch_admm_fused(a, PREC_F32, PREC_F32, s);
         }
+        const int nb = pdr ? pdr_plain_blocks(g) : cp ? cp_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
         if (check) {
-            const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
             launch_reduce_check(partials, nb, &misc->res_check, rows, params->tol, &misc->done, &misc->iters, 10, s);
         }
     }
@@ -1027,7 +1051,7 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
         launch_parity_fix(from, to, g, PREC_F32, PREC_F32, params->tol > 0.0 ? &misc->done : nullptr, 0, s);
     }
     if (res2) {
-        const int nb = pdr ? pdr_plain_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
+        const int nb = pdr ? pdr_plain_blocks(g) : cp ? cp_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
         if (iters > 0) launch_sum(partials, nb, &misc->res_final, s);
         Misc m;
         OF_CUDA(cudaMemcpyAsync(&m, misc, sizeof(Misc), cudaMemcpyDeviceToHost, s));
@@ -1042,12 +1066,17 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
 
 of_status of_admm_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H, int W, int pitch,
                           float a_tilde, const of_params *params, int iters, void *scratch, double *res2, void *stream) {
-    return iterate_common(f, Ix, Iy, It, H, W, pitch, a_tilde, params, iters, scratch, res2, stream, false);
+    return iterate_common(f, Ix, Iy, It, H, W, pitch, a_tilde, params, iters, scratch, res2, stream, KIND_ADMM);
 }
 
 of_status of_pdr_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H, int W, int pitch,
                          const of_params *params, int iters, void *scratch, double *res2, void *stream) {
-    return iterate_common(f, Ix, Iy, It, H, W, pitch, 1.f, params, iters, scratch, res2, stream, true);
+    return iterate_common(f, Ix, Iy, It, H, W, pitch, 1.f, params, iters, scratch, res2, stream, KIND_PDR);
+}
+
+of_status of_cp_iterate(of_fields f, const float *Ix, const float *Iy, const float *It, int H, int W, int pitch,
+                        const of_params *params, int iters, void *scratch, double *res2, void *stream) {
+    return iterate_common(f, Ix, Iy, It, H, W, pitch, 1.f, params, iters, scratch, res2, stream, KIND_CP);
 }
 
 of_status of_energy(const float *w, const float *u, const float *v, const float *s, const float *Ix, const float *Iy,

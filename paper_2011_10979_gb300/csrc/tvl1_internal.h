@@ -30,7 +30,8 @@ struct Fields {
 struct Coefs {
     float lambda, beta, c, a, r, rho, sigma, tau;
     float a_tilde_fixed;  // > 0: used as a~; otherwise a~ = max(ms_max, 1e-12)
-    int method;           // 0 rpADMMI, 1 rpADMMII, 2 pDR
+    float cp_tau, cp_sigma;  // ALG1 dual and primal steps
+    int method;           // 0 rpADMMI, 1 rpADMMII, 2 pDR, 3 ALG1
     int gs_sweeps;
 };
 
@@ -159,6 +160,12 @@ int pdr_fused_blocks(Geom g);
 void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 int pdr_plain_blocks(Geom g);
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------- ALG1 (k_cp.cu)
+// One fused kernel per iteration, reads args.in and writes args.out (ping-pong).  Batched form
+// as the pDR engines (blockIdx.z = pair, args.g = the largest geometry, parity selects buffers).
+int cp_blocks(Geom g);
+void launch_cp(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions (k_reduce.cu)
 // Sums `n` partials in a fixed order into out[0]; if tol > 0 and the normalised residual

@@ -16,14 +16,15 @@ LIB_PATH = os.path.join(_PKG, "libtvl1flow.so")
 _lib = None
 
 OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_ETIMEOUT, OF_ENUMERIC, OF_EBUSY = range(7)
-OF_PADMM_I, OF_PADMM_II, OF_PDR = 0, 1, 2
+OF_PADMM_I, OF_PADMM_II, OF_PDR, OF_CP = 0, 1, 2, 3
 OF_PREC_FP32, OF_PREC_FP16, OF_PREC_BF16 = 0, 1, 2
 OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT = 0, 1, 2, 3
 
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
            "of_solve_kernel_count", "of_solve",
            "of_solve_host", "of_solve_batch", "of_pyr_down", "of_upsample", "of_derivatives",
-           "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_fields_bytes", "of_energy",
+           "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_cp_iterate",
+           "of_fields_bytes", "of_energy",
            "of_server_start", "of_server_submit", "of_server_poll", "of_server_stop")
 
 
@@ -41,7 +42,8 @@ class of_params(ctypes.Structure):
                 ("levels", ctypes.c_int), ("warps", ctypes.c_int), ("iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_last_warp", ctypes.c_int),
                 ("fp32_flow", ctypes.c_int),
-                ("engine", ctypes.c_int), ("out_level", ctypes.c_int)]
+                ("engine", ctypes.c_int), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_float),
+                ("cp_sigma", ctypes.c_float)]
 
 
 class of_stats(ctypes.Structure):
@@ -87,6 +89,7 @@ def lib():
             "of_admm_iterate": (i, [of_fields, vp, vp, vp, i, i, i, f, P(of_params), i, vp, P(d), vp]),
             "of_admm_iterate_noalloc": (i, [of_fields, vp, vp, vp, i, i, i, f, P(of_params), i, P(d), vp]),
             "of_pdr_iterate": (i, [of_fields, vp, vp, vp, i, i, i, P(of_params), i, vp, P(d), vp]),
+            "of_cp_iterate": (i, [of_fields, vp, vp, vp, i, i, i, P(of_params), i, vp, P(d), vp]),
             "of_fields_bytes": (sz, [i, i]),
             "of_energy": (i, [vp, vp, vp, vp, vp, vp, vp, i, i, i, f, f, P(d), P(d), vp]),
             "of_server_start": (i, [vp, P(of_params), sz, i]),
@@ -296,6 +299,17 @@ def of_pdr_iterate(state: dict, Ix, Iy, It, params: of_params, iters, want_res=T
     check(lib().of_pdr_iterate(_fields(state), _ptr(Ix), _ptr(Iy), _ptr(It), H, W, Ix.stride(0),
                                ctypes.byref(params), iters, _ptr(scratch), ctypes.byref(res) if want_res else None,
                                _stream(stream)))
+    return res.value
+
+
+def of_cp_iterate(state: dict, Ix, Iy, It, params: of_params, iters, want_res=True, stream=None):
+    import torch
+    H, W = Ix.shape
+    scratch = torch.empty(lib().of_fields_bytes(H, Ix.stride(0)), dtype=torch.uint8, device=Ix.device)
+    res = ctypes.c_double(0.0)
+    check(lib().of_cp_iterate(_fields(state), _ptr(Ix), _ptr(Iy), _ptr(It), H, W, Ix.stride(0),
+                              ctypes.byref(params), iters, _ptr(scratch), ctypes.byref(res) if want_res else None,
+                              _stream(stream)))
     return res.value
 
 

@@ -163,6 +163,38 @@ def test_pdr_iterations(ctx, orc, H, W, beta, engine, sweeps):
     assert abs(res_gpu - res_ref) <= 1e-3 * max(res_ref, 1e-6) + 1e-7
 
 
+@pytest.mark.parametrize("H,W", ITER_SHAPES)
+@pytest.mark.parametrize("beta", [0.05, 0.0])
+def test_cp_iterations(ctx, orc, H, W, beta):
+    """ALG1 (Sec. 4, Chambolle-Pock with constant steps): the fused kernel against the oracle's
+    step, iterated from a random state."""
+    rng = np.random.default_rng(H * 29 + W)
+    lam = 0.3
+    st = _random_state(H, W, rng, lam, beta, pdr=True)
+    Ix, Iy, It = (rng.normal(size=(H, W)).astype(np.float32) * s for s in (0.4, 0.4, 0.2))
+    iters = 23
+    P = flow.default_params(method=3, lam=lam, beta=beta)
+    fields = ("w", "u", "v", "p1", "p2", "q11", "q12", "q21", "q22", "wb", "ub", "vb")
+    dev = {k: cu(st[k]) for k in fields}
+    if beta == 0.0:
+        for k in ("w", "p1", "p2", "wb"):
+            dev[k] = None
+    res_gpu = flow.of_cp_iterate(dev, cu(Ix), cu(Iy), cu(It), P, iters)
+    ost = orc.State.zeros(H, W)
+    for k in orc.STATE_FIELDS:
+        if k in st:
+            ost[k] = st[k].astype(np.float64)
+    OP = orc.Params(method=3, lam=lam, beta=beta)
+    for _ in range(iters):
+        res_ref = orc.cp_step(ost, Ix, Iy, It, OP)
+    for k in fields:
+        if dev[k] is None:
+            continue
+        err = np.max(np.abs(np64(dev[k]) - ost[k]))
+        assert err < 1e-4, (k, err)
+    assert abs(res_gpu - res_ref) <= 1e-3 * max(res_ref, 1e-6) + 1e-7
+
+
 def test_energy(ctx, orc):
     rng = np.random.default_rng(5)
     H, W = 40, 50
@@ -180,6 +212,7 @@ METHODS = {
     "rpadmm2": dict(method=1, rho=1.9),
     "zach": dict(method=0, r=1.0, beta=0.0),
     "pdr": dict(method=2),
+    "alg1": dict(method=3),
 }
 
 
@@ -230,7 +263,7 @@ def test_schedule_degenerate_sizes(ctx, orc, H, W):
     I0 = rng.random((H, W)).astype(np.float32)
     I1 = np.roll(I0, 1, axis=1) if W > 1 else I0 * 0.9
     pr = synth.Pair(I0, I1.astype(np.float32), None, None)
-    for name in ("padmm", "pdr"):
+    for name in ("padmm", "pdr", "alg1"):
         u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 3, 2, 7, 1.0, METHODS[name])
         mu, mv, epe = _flow_errors(u, v, ru, rv)
         assert mu <= 1e-3 and mv <= 1e-3, (name, mu, mv)
@@ -246,7 +279,7 @@ def test_zero_iterations_and_identity_pair(ctx, orc):
     assert float(u.abs().max()) == 0.0 and float(v.abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("name", ["padmm", "pdr"])
+@pytest.mark.parametrize("name", ["padmm", "pdr", "alg1"])
 def test_stopping_rule(ctx, orc, name):
     pr = synth.sinusoid_pair()
     extra = dict(METHODS[name], tol=3e-3)
@@ -282,13 +315,14 @@ def _batch_pairs():
 
 
 @pytest.mark.parametrize("name,prec,tol", [("padmm", 0, 0.0), ("rpadmm2", 0, 0.0), ("zach", 0, 0.0), ("pdr", 0, 0.0),
-                                           ("padmm", 2, 0.0), ("pdr", 1, 0.0), ("padmm", 0, 3e-3), ("pdr", 0, 3e-3)])
+                                           ("padmm", 2, 0.0), ("pdr", 1, 0.0), ("padmm", 0, 3e-3), ("pdr", 0, 3e-3),
+                                           ("alg1", 0, 0.0), ("alg1", 2, 3e-3)])
 @pytest.mark.parametrize("engine", [flow.OF_ENGINE_FUSED, flow.OF_ENGINE_STREAM])
 def test_batch_equals_single(ctx, name, prec, tol, engine):
     """Uneven sizes solved in one batch (one work-list launch per iteration, or one level-resident
     launch per warp) give bitwise the results of the separate single-pair solves."""
-    if name == "pdr" and engine == flow.OF_ENGINE_STREAM:
-        pytest.skip("pDR has one fused engine")
+    if name in ("pdr", "alg1") and engine == flow.OF_ENGINE_STREAM:
+        pytest.skip("pDR and ALG1 have one fused engine")
     pairs = _batch_pairs()
     P = flow.default_params(lam=2.0, precision=prec, tol=tol, iters=40, engine=engine, **METHODS[name])
     us, vs, sts = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], P)
@@ -302,7 +336,8 @@ def test_batch_equals_single(ctx, name, prec, tol, engine):
 def test_invalid_arguments(ctx):
     pr = synth.sinusoid_pair()
     for bad in (dict(levels=0), dict(lam=-1.0), dict(eta=1.5), dict(method=7), dict(r=2.0),
-                dict(method=1, rho=2.5), dict(precision=1, engine=flow.OF_ENGINE_PLAIN), dict(out_level=3)):
+                dict(method=1, rho=2.5), dict(precision=1, engine=flow.OF_ENGINE_PLAIN), dict(out_level=3),
+                dict(method=3, cp_tau=0.0), dict(method=3, engine=flow.OF_ENGINE_PLAIN), dict(method=4)):
         with pytest.raises(flow.OfError) as e:
             flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), flow.default_params(**bad))
         assert e.value.status == flow.OF_EINVAL
@@ -320,7 +355,7 @@ def test_schedule_640x480_full(ctx, orc):
 
 
 @pytest.mark.parametrize("prec", [flow.OF_PREC_FP16, flow.OF_PREC_BF16])
-@pytest.mark.parametrize("name", ["padmm", "pdr"])
+@pytest.mark.parametrize("name", ["padmm", "pdr", "alg1"])
 @pytest.mark.parametrize("fp32_flow", [1, 0])
 def test_precision_64x48(ctx, orc, prec, name, fp32_flow):
     """16-bit storage with FP32 arithmetic and the finest level's last warp in FP32.  With the
