@@ -22,12 +22,13 @@ int forced_rows_per_warp() {
 }  // namespace
 
 int admm_fused_rows_per_warp(long strip_rows) {
-    // rows per warp: the tallest strips (least halo: (TY+3)/TY) that still give about eight warps
-    // per SM; on small levels a warp's TY + 3 row steps are the latency of the whole iteration, so
-    // there strips of one or two rows trade redundant halo work for a short chain
+    // rows per warp: 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller
+    // levels a warp's TY + 3 row steps are the latency of the whole iteration, so there strips of
+    // two or one row trade redundant halo work for a short chain.  Taller strips (16, 32) have
+    // less halo but a longer chain and measured slower at every size from 640x480 to 1920x1080.
     if (const int f = forced_rows_per_warp()) return f;
     const long want = 8L * 152;
-    const int cand[4] = {32, 8, 2, 1};
+    const int cand[3] = {8, 2, 1};
     for (int t : cand)
         if (strip_rows / t >= want) return t;
     return 1;
