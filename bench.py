@@ -370,6 +370,26 @@ def solvers_measure(flow, torch, dev, I0, I1, pr):
             vt = torch.from_numpy(pr.v_true.astype(np.float32)).to(dev)
             r["epe_vs_true_px"] = float(torch.hypot(u - ut, v - vt).mean())
         out[name] = r
+    # the per-pixel s-preconditioner (a~_ij = M_s(ij)) against the scalar a~ = max M_s, with the
+    # stopping rule on (tol 1e-3): iterations run, time and accuracy
+    for mode, name in ((0, "pADMM tol=1e-3, scalar a~"), (1, "pADMM tol=1e-3, per-pixel a~")):
+        P = flow.default_params(lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS, tol=1e-3,
+                                a_tilde_mode=mode)
+        u, v, _, st = flow.of_solve(ctx, I0, I1, P)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            flow.of_solve(ctx, I0, I1, P, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 3
+        r = {"ms_per_solve": ms, "flows_per_s": 1e3 / ms, "iters_run": st["iters_run"], "energy": st["energy"]}
+        if pr.u_true is not None:
+            ut = torch.from_numpy(pr.u_true.astype(np.float32)).to(dev)
+            vt = torch.from_numpy(pr.v_true.astype(np.float32)).to(dev)
+            r["epe_vs_true_px"] = float(torch.hypot(u - ut, v - vt).mean())
+        out[name] = r
     ctx.close()
     return out
 

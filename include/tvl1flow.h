@@ -93,6 +93,10 @@ typedef struct {
     int out_level;       /* stop after this pyramid level and return its flow (0 = finest)     */
     float cp_tau;        /* ALG1 dual step (Sec. 4: 0.1)                                        */
     float cp_sigma;      /* ALG1 primal step; Sec. 4's garbled rule read as 1 / (8 cp_tau) = 1.25 */
+    int a_tilde_mode;    /* ADMM s-block preconditioner: 0 = one a~ per warp (a_tilde, or
+                            ||M_s|| = max M_s, Prop. 3.1); 1 = the per-pixel diagonal
+                            a~_ij = max(M_s(ij), 1e-12), which keeps c(diag(a~) - M_s) positive
+                            semidefinite because M_s is diagonal (an extension, not in the paper) */
 } of_params;
 
 typedef struct {

@@ -13,6 +13,8 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
   srbgs ................. pinned (red-black GS property, convergence to a direct sparse solve)
   admm_step ............. pinned (subproblem optimality, special cases, strong duality)
   pdr_step .............. pinned (same minimum as ADMM, dual certificate, SRBGS limit)
+  admm_step, per-pixel a~ pinned (s-subproblem solution with the diagonal preconditioner;
+                          same certified minimum)
   cp_step (ALG1) ........ pinned (dual step = projection, primal step = prox optimality,
                           same certified minimum as ADMM at a fixed linearisation)
   pyramid / upsample .... pinned only by exactness properties (constants, ramps, ratios)
@@ -57,7 +59,7 @@ class _Params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("gs_sweeps", ctypes.c_int), ("eta", ctypes.c_double),
                 ("levels", ctypes.c_int), ("warps", ctypes.c_int), ("iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_double),
-                ("cp_sigma", ctypes.c_double)]
+                ("cp_sigma", ctypes.c_double), ("a_tilde_mode", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -87,11 +89,13 @@ class Params:
     out_level: int = 0
     cp_tau: float = 0.1      # ALG1 dual step (Sec. 4)
     cp_sigma: float = 1.25   # ALG1 primal step 1 / (8 cp_tau) (Sec. 4, reading of the step rule)
+    a_tilde_mode: int = 0    # 0: a~ = max M_s per warp (Prop. 3.1); 1: per-pixel a~_ij = M_s(ij)
 
     def _c(self) -> _Params:
         return _Params(self.method, self.lam, self.beta, self.c, self.a, self.a_tilde, self.r,
                        self.rho, self.sigma, self.tau, self.gs_sweeps, self.eta, self.levels,
-                       self.warps, self.iters, self.tol, self.out_level, self.cp_tau, self.cp_sigma)
+                       self.warps, self.iters, self.tol, self.out_level, self.cp_tau, self.cp_sigma,
+                       self.a_tilde_mode)
 
 
 _D = ctypes.POINTER(ctypes.c_double)

@@ -310,6 +310,7 @@ typedef struct {
     int out_level;     /* stop after this pyramid level and return its flow */
     double cp_tau;     /* ALG1 dual step */
     double cp_sigma;   /* ALG1 primal step */
+    int a_tilde_mode;  /* 0: one a~ per warp (the paper's ||M_s||); 1: per-pixel a~_ij = M_s(ij) */
 } orc_params;
 
 typedef struct {
@@ -392,18 +393,22 @@ double orc_admm_step(int H, int W, orc_state *st, const double *Ix, const double
     orc_div(H, W, nq11, nq12, dq1);
     orc_div(H, W, nq21, nq22, dq2);
 
-    /* s-update with the old multipliers Lambda^k and the new y^{k+1}, then P_s */
+    /* s-update with the old multipliers Lambda^k and the new y^{k+1}, then P_s.
+     * Per-pixel preconditioner (a_tilde_mode 1): M_s is diagonal, so the s-block proximal matrix
+     * c(diag(a~) - M_s) stays positive semidefinite with a~_ij = M_s(ij) (floored at 1e-12),
+     * the pointwise form of the paper's a~ = ||M_s|| (Prop. 3.1). */
     double res2 = 0.0;
     for (size_t k = 0; k < N; ++k) {
         double ms = beta * beta + Ix[k] * Ix[k] + Iy[k] * Iy[k];
+        double a_tilde_k = P->a_tilde_mode == 1 ? (ms > 1e-12 ? ms : 1e-12) : a_tilde;
         double lin = It[k] + Ix[k] * st->u[k] + Iy[k] * st->v[k] + (has_w ? beta * st->w[k] : 0.0);
         double divterm = Ix[k] * dq1[k] + Iy[k] * dq2[k] + (has_w ? beta * dp[k] : 0.0);
         double s_old = st->s[k], s_new;
         if (P->method == 1) {
             double rho = P->rho;
-            s_new = (1.0 - rho * ms / a_tilde) * s_old + (lin + c * rho * divterm) / (a_tilde * c);
+            s_new = (1.0 - rho * ms / a_tilde_k) * s_old + (lin + c * rho * divterm) / (a_tilde_k * c);
         } else {
-            s_new = (1.0 - ms / a_tilde) * s_old + (lin + c * divterm) / (a_tilde * c);
+            s_new = (1.0 - ms / a_tilde_k) * s_old + (lin + c * divterm) / (a_tilde_k * c);
         }
         {
             double f = fabs(s_new) / P->lambda;

@@ -84,10 +84,11 @@ __global__ void k_supdate_plain(IterArgs A, const float *dp, const float *dq1, c
         auto F = [&](int f) { return (float *)A.in.f[f]; };
         const float ix = ((const float *)A.Ix)[o], iy = ((const float *)A.Iy)[o], it = ((const float *)A.It)[o];
         const float beta = A.k.beta, c = A.k.c, lam = A.k.lambda, rho = A.k.rho;
-        const float at = a_tilde_of(A.k, A.ms_max);
         const float s_old = F(F_S)[o];
         float w = has_w ? F(F_W)[o] : 0.f, u = F(F_U)[o], v = F(F_V)[o];
         const float ms = beta * beta + ix * ix + iy * iy;
+        // a~: one value per warp, or the per-pixel diagonal a~_ij = M_s(ij)
+        const float at = A.k.a_tilde_mode == 1 ? fmaxf(ms, 1e-12f) : a_tilde_of(A.k, A.ms_max);
         const float lin = it + ix * u + iy * v + (has_w ? beta * w : 0.f);
         const float divt = ix * dq1[o] + iy * dq2[o] + (has_w ? beta * dp[o] : 0.f);
         float s_new;

@@ -8,9 +8,11 @@
 
 namespace tvl1 {
 
-// Step constants of one warp: 1/a, 1/c, beta, 1/a~, 1/(a~ c), c, lambda, rho, 1 - rho, r c.
+// Step constants of one warp: 1/a, 1/c, beta, 1/a~, 1/(a~ c), c, lambda, rho, 1 - rho, r c, and
+// whether a~ is the per-pixel diagonal a~_ij = M_s(ij) instead of one value per warp.
 struct StepK {
     float inv_a, inv_c, beta, inv_at, inv_atc, cc, lam, rho, omr, rc;
+    int per_pixel;
 };
 
 __device__ __forceinline__ StepK step_coefs(const Coefs &K, float at) {
@@ -25,6 +27,7 @@ __device__ __forceinline__ StepK step_coefs(const Coefs &K, float at) {
     s.rho = K.rho;
     s.omr = 1.f - K.rho;
     s.rc = K.r * K.c;
+    s.per_pixel = K.a_tilde_mode == 1;
     return s;
 }
 
@@ -69,6 +72,8 @@ __device__ __forceinline__ void y_update_q(float q11, float q12, float q21, floa
 //   s^{k+1} = P_s[(1 - M_s / a~) s^k + (l + c t) / (a~ c)]            (VARIANT 0: rpADMMI / pADMM)
 //   s^{k+1} = P_s[(1 - rho M_s / a~) s^k + (l + c rho t) / (a~ c)]    (VARIANT 1: rpADMMII)
 // with M_s = beta^2 + Ix^2 + Iy^2, l = It + Ix u + Iy v + beta w, t = Ix dq1n + Iy dq2n + beta dpn;
+// With the per-pixel preconditioner a~ is M_s at the pixel (floored at 1e-12): M_s is diagonal,
+// so the s-block proximal matrix c(diag(a~) - M_s) stays positive semidefinite;
 // then Lambda = (w, u, v) -= r c (A s^{k+1} - div y^{k+1}) (VARIANT 0) or
 // Lambda -= c (A s^{k+1} - rho div y^{k+1} - (1 - rho) A s^k) (VARIANT 1), A s = (beta, Ix, Iy) s.
 // Updates w, u, v in place, returns s^{k+1} in s_new and the squared constraint residual
@@ -82,9 +87,15 @@ __device__ __forceinline__ float finish_pixel(float ix, float iy, float it, floa
     const float lin = HAS_W ? fmaf(beta, w, lin0) : lin0;
     const float divt0 = fmaf(iy, dq2n, ix * dq1n);
     const float divt = HAS_W ? fmaf(beta, dpn, divt0) : divt0;
+    float inv_at = K.inv_at, inv_atc = K.inv_atc;
+    if (K.per_pixel) {  // uniform over the launch
+        const float at = fmaxf(ms, 1e-12f);
+        inv_at = __frcp_rn(at);
+        inv_atc = __frcp_rn(at * K.cc);
+    }
     float s;
-    if (VARIANT == 0) s = fmaf(fmaf(K.cc, divt, lin), K.inv_atc, fmaf(-ms, K.inv_at, 1.f) * s_old);
-    else s = fmaf(fmaf(K.cc * K.rho, divt, lin), K.inv_atc, fmaf(-K.rho * ms, K.inv_at, 1.f) * s_old);
+    if (VARIANT == 0) s = fmaf(fmaf(K.cc, divt, lin), inv_atc, fmaf(-ms, inv_at, 1.f) * s_old);
+    else s = fmaf(fmaf(K.cc * K.rho, divt, lin), inv_atc, fmaf(-K.rho * ms, inv_at, 1.f) * s_old);
     s = fminf(fmaxf(s, -K.lam), K.lam);  // P_s: projection onto |s| <= lambda
     s_new = s;
     const float cw = HAS_W ? fmaf(beta, s, -dpn) : 0.f;

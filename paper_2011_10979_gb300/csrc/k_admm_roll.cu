@@ -22,15 +22,18 @@ int forced_rows_per_warp() {
 }  // namespace
 
 int admm_fused_rows_per_warp(long strip_rows) {
-    // rows per warp: 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller
-    // levels a warp's TY + 3 row steps are the latency of the whole iteration, so there strips of
-    // two or one row trade redundant halo work for a short chain.  Taller strips (16, 32) have
-    // less halo but a longer chain and measured slower at every size from 640x480 to 1920x1080.
+    // rows per warp.  Launches with ample parallelism (batches: >= 64 warps per SM at 32 rows)
+    // take 32 (halo (32+3)/32): they are bandwidth-bound and the halo re-reads dominate.  Otherwise
+    // 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller levels a warp's
+    // TY + 3 row steps are the latency of the whole iteration, so there strips of two or one row
+    // trade redundant halo work for a short chain.  (Single pairs from 640x480 to 1920x1080
+    // measured fastest at 8; a 256-pair batch 5% faster at 32 than at 8.)
     if (const int f = forced_rows_per_warp()) return f;
-    const long want = 8L * 152;
+    const long sms = 152;
+    if (strip_rows / 32 >= 64L * sms) return 32;
     const int cand[3] = {8, 2, 1};
     for (int t : cand)
-        if (strip_rows / t >= want) return t;
+        if (strip_rows / t >= 8L * sms) return t;
     return 1;
 }
 

@@ -95,6 +95,7 @@ of_status validate(const of_params *p, int H, int W) {
     if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(OF_EINVAL, "tol must be >= 0");
     if (p->precision < 0 || p->precision > 2) return fail(OF_EINVAL, "unknown precision");
     if (p->engine < 0 || p->engine > 3) return fail(OF_EINVAL, "unknown engine");
+    if (p->a_tilde_mode < 0 || p->a_tilde_mode > 1) return fail(OF_EINVAL, "a_tilde_mode must be 0 or 1");
     if (p->engine == OF_ENGINE_PLAIN && p->precision != OF_PREC_FP32)
         return fail(OF_EINVAL, "the plain engine runs in FP32 only");
     if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
@@ -221,6 +222,7 @@ Coefs coefs_of(const of_params *p) {
     k.a_tilde_fixed = p->a_tilde;
     k.cp_tau = p->cp_tau;
     k.cp_sigma = p->cp_sigma;
+    k.a_tilde_mode = p->a_tilde_mode;
     k.method = p->method;
     k.gs_sweeps = p->gs_sweeps;
     return k;
@@ -732,6 +734,7 @@ void of_default_params(of_params *p) {
     p->out_level = 0;
     p->cp_tau = 0.1f;
     p->cp_sigma = 1.25f;
+    p->a_tilde_mode = 0;
 }
 
 of_status of_create(of_ctx **out, int device, size_t hbm_budget_bytes) {

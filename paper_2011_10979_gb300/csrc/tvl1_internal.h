@@ -31,6 +31,7 @@ struct Coefs {
     float lambda, beta, c, a, r, rho, sigma, tau;
     float a_tilde_fixed;  // > 0: used as a~; otherwise a~ = max(ms_max, 1e-12)
     float cp_tau, cp_sigma;  // ALG1 dual and primal steps
+    int a_tilde_mode;     // 0: a~ per warp; 1: per-pixel a~_ij = max(M_s(ij), 1e-12)
     int method;           // 0 rpADMMI, 1 rpADMMII, 2 pDR, 3 ALG1
     int gs_sweeps;
 };

@@ -43,7 +43,7 @@ class of_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_last_warp", ctypes.c_int),
                 ("fp32_flow", ctypes.c_int),
                 ("engine", ctypes.c_int), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_float),
-                ("cp_sigma", ctypes.c_float)]
+                ("cp_sigma", ctypes.c_float), ("a_tilde_mode", ctypes.c_int)]
 
 
 class of_stats(ctypes.Structure):

@@ -99,18 +99,20 @@ ITER_SHAPES = [(1, 1), (1, 9), (9, 1), (7, 5), (33, 17), (48, 64), (100, 130)]
 
 
 @pytest.mark.parametrize("H,W", ITER_SHAPES)
-@pytest.mark.parametrize("variant", ["padmm", "rpadmm1", "rpadmm2", "zach"])
+@pytest.mark.parametrize("variant", ["padmm", "rpadmm1", "rpadmm2", "zach", "padmm_pp", "rpadmm2_pp"])
 @pytest.mark.parametrize("engine", [flow.OF_ENGINE_FUSED, flow.OF_ENGINE_PLAIN])
 def test_admm_iterations(ctx, orc, H, W, variant, engine):
+    """31 iterations from a random state against the oracle; "_pp": the per-pixel s-preconditioner."""
     rng = np.random.default_rng(H * 31 + W)
     lam, beta = 0.3, (0.0 if variant == "zach" else 0.05)
-    method = 1 if variant == "rpadmm2" else 0
+    method = 1 if variant.startswith("rpadmm2") else 0
     r = 1.618 if variant == "rpadmm1" else 1.0
+    mode = 1 if variant.endswith("_pp") else 0
     st = _random_state(H, W, rng, lam, beta)
     Ix, Iy, It = (rng.normal(size=(H, W)).astype(np.float32) * s for s in (0.4, 0.4, 0.2))
     at = float((beta ** 2 + Ix.astype(np.float64) ** 2 + Iy.astype(np.float64) ** 2).max()) + 1e-3
     iters = 31
-    P = flow.default_params(method=method, lam=lam, beta=beta, r=r, rho=1.9, engine=engine)
+    P = flow.default_params(method=method, lam=lam, beta=beta, r=r, rho=1.9, engine=engine, a_tilde_mode=mode)
     fields = ("w", "u", "v", "p1", "p2", "q11", "q12", "q21", "q22", "s")
     dev = {k: cu(st[k]) for k in fields}
     if beta == 0.0:
@@ -120,7 +122,7 @@ def test_admm_iterations(ctx, orc, H, W, variant, engine):
     ost = orc.State.zeros(H, W)
     for k in orc.STATE_FIELDS:
         ost[k] = st[k].astype(np.float64)
-    OP = orc.Params(method=method, lam=lam, beta=beta, r=r, rho=1.9)
+    OP = orc.Params(method=method, lam=lam, beta=beta, r=r, rho=1.9, a_tilde_mode=mode)
     for _ in range(iters):
         res_ref = orc.admm_step(ost, Ix, Iy, It, float(np.float32(at)), OP)
     for k in fields:
@@ -213,6 +215,7 @@ METHODS = {
     "zach": dict(method=0, r=1.0, beta=0.0),
     "pdr": dict(method=2),
     "alg1": dict(method=3),
+    "padmm_pp": dict(method=0, r=1.0, a_tilde_mode=1),
 }
 
 

@@ -111,14 +111,16 @@ def test_srbgs_is_affine(orc):
 # ------------------------------------------------------------------------ ADMM updates
 @pytest.mark.parametrize("beta", [0.05, 0.0])
 @pytest.mark.parametrize("r", [1.0, 1.618])
-def test_rpadmm1_step_solves_its_subproblems(orc, beta, r):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rpadmm1_step_solves_its_subproblems(orc, beta, r, mode):
     """eq. (aug:pre1:vector): y^{k+1} maximises L_c(Lambda^k; y, s^k) - 1/2||y - y^k||^2_{acI - c grad grad^*}
-    over |p|, |q| <= 1; s^{k+1} maximises L_c(Lambda^k; y^{k+1}, s) - 1/2||s - s^k||^2_{a~cI - cM_s}
-    over |s| <= lambda (with <I_t, s> counted once); Lambda^{k+1} = Lambda^k - rc(A s + B y)."""
+    over |p|, |q| <= 1; s^{k+1} maximises L_c(Lambda^k; y^{k+1}, s) - 1/2||s - s^k||^2_{c(diag(a~) - M_s)}
+    over |s| <= lambda (with <I_t, s> counted once), a~ one value (mode 0) or the per-pixel
+    a~_ij = M_s(ij) (mode 1); Lambda^{k+1} = Lambda^k - rc(A s + B y)."""
     H, W = 7, 6
     rng, d, beta, lam = _random_problem(H, W, 11, beta=beta)
     Ix, Iy, It = (d[k].ravel() for k in ("Ix", "Iy", "It"))
-    P = orc.Params(method=0, lam=lam, beta=beta, c=0.05, a=8.0, r=r)
+    P = orc.Params(method=0, lam=lam, beta=beta, c=0.05, a=8.0, r=r, a_tilde_mode=mode)
     a, c = P.a, P.c
     st = _random_state(orc, rng, H, W, lam, beta)
     Ms = beta ** 2 + Ix ** 2 + Iy ** 2
@@ -168,7 +170,8 @@ def test_rpadmm1_step_solves_its_subproblems(orc, beta, r):
     for lam_name, comps, coef in blocks:
         cons = coef * s0 + ops.Bt(yn[comps])
         grad_s += coef * (old[lam_name].ravel() - c * cons)
-    s_pred = np.clip(s0 + grad_s / (at * c), -lam, lam)
+    at_px = np.maximum(Ms, 1e-12) if mode == 1 else at
+    s_pred = np.clip(s0 + grad_s / (at_px * c), -lam, lam)
     np.testing.assert_allclose(st["s"].ravel(), s_pred, atol=1e-12)
     # --- multipliers
     s1 = st["s"].ravel()
@@ -407,6 +410,37 @@ def test_solvers_reach_the_same_minimum_with_a_dual_certificate(orc):
     ebf = _primal_energy_dense(H, W, Xbf, d, beta, lam)
     assert ebf >= ref * (1 - 1e-9)
     assert ebf - ref < 5e-4 * ref
+
+
+@pytest.mark.slow
+def test_per_pixel_preconditioner_reaches_the_certified_minimum(orc):
+    """The per-pixel s-preconditioner a~_ij = M_s(ij) keeps c(diag(a~) - M_s) >= 0 (M_s is
+    diagonal), so pADMM and rpADMMII still converge to the saddle point: residual -> 0, primal
+    energy = dual value (strong duality) = the scalar-a~ minimum.  On this problem pADMM needs
+    about half the iterations of the scalar a~ = max M_s to reach a residual of 1e-6."""
+    H, W = 8, 8
+    rng = np.random.default_rng(21)
+    y_, x_ = np.mgrid[0:H, 0:W].astype(float)
+    img = np.sin(0.9 * x_ + 0.3) + np.cos(0.7 * y_ - 0.2 * x_)
+    d = dict(Ix=0.3 * np.cos(0.9 * x_ + 0.3), Iy=-0.2 * np.sin(0.7 * y_ - 0.2 * x_),
+             It=0.15 * img + 0.05 * rng.normal(size=(H, W)))
+    beta, lam = 0.05, 0.8
+    at = float((beta ** 2 + d["Ix"] ** 2 + d["Iy"] ** 2).max())
+    st = orc.State.zeros(H, W)
+    orc.inner(st, d["Ix"], d["Iy"], d["It"], at, orc.Params(method=0, lam=lam, beta=beta), 150000)
+    ref = orc.energy(st["w"], st["u"], st["v"], d["Ix"], d["Iy"], d["It"], beta, lam)
+    for kw in (dict(method=0), dict(method=1, rho=1.9)):
+        st = orc.State.zeros(H, W)
+        n, res = orc.inner(st, d["Ix"], d["Iy"], d["It"], at, orc.Params(lam=lam, beta=beta, a_tilde_mode=1, **kw), 150000)
+        E = orc.energy(st["w"], st["u"], st["v"], d["Ix"], d["Iy"], d["It"], beta, lam)
+        assert res < 1e-8, (kw, res)
+        assert abs(E - ref) < 1e-7 * ref and abs(E - orc.dual_value(d["It"], st["s"])) < 1e-7 * E, (kw, E, ref)
+    runs = {}
+    for mode in (0, 1):
+        st = orc.State.zeros(H, W)
+        runs[mode], _ = orc.inner(st, d["Ix"], d["Iy"], d["It"], at,
+                                  orc.Params(method=0, lam=lam, beta=beta, a_tilde_mode=mode, tol=1e-6), 200000)
+    assert runs[1] < 0.7 * runs[0], runs
 
 
 def test_zero_motion_pair_stays_zero(orc):
