@@ -1,5 +1,5 @@
 // k_admm_math.cuh -- the per-pixel arithmetic of one ADMM iteration (Sec. 3.1.1), shared by the
-// row-streaming kernel (k_admm_roll.cuh) and the level-resident kernel (k_admm_resident.cu).
+// row-streaming kernel (k_admm_roll.cuh) and the level-resident kernel (k_resident.cu).
 // Every product-sum is an explicit fmaf, so both kernels round every pixel alike (FP32).
 #pragma once
 #include <math.h>

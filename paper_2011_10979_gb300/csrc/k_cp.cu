@@ -13,6 +13,7 @@
 // buf[parity ^ 1]; its partials occupy cp_blocks(args.g) slots from z * cp_blocks(args.g).
 #include <math.h>
 
+#include "k_cp_math.cuh"
 #include "tvl1_device.cuh"
 
 namespace tvl1 {
@@ -20,9 +21,6 @@ namespace tvl1 {
 namespace {
 
 constexpr int PX = 32, PY = 8;
-
-// 1 / max(1, sqrt(n2)): the scale of the projection onto the unit ball.
-__device__ __forceinline__ float ball_scale_cp(float n2) { return n2 > 1.f ? rsqrtf(n2) : 1.f; }
 
 template <typename T, typename TF, bool HAS_W>
 __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
@@ -65,24 +63,20 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
             const bool hx = b < W - 1, hy = a < H - 1;
             auto gx = [&](int f) { return hx ? ldT<TF>(in.f[f], o + 1) - ldT<TF>(in.f[f], o) : 0.f; };
             auto gy = [&](int f) { return hy ? ldT<TF>(in.f[f], o + P) - ldT<TF>(in.f[f], o) : 0.f; };
-            if (HAS_W) {
-                const float t1 = fmaf(tau, gx(F_WB), ldT<T>(in.f[F_P1], o));
-                const float t2 = fmaf(tau, gy(F_WB), ldT<T>(in.f[F_P2], o));
-                const float f = ball_scale_cp(fmaf(t1, t1, t2 * t2));
-                y[0] = t1 * f;
-                y[1] = t2 * f;
-            } else {
-                y[0] = y[1] = 0.f;
-            }
-            const float t11 = fmaf(tau, gx(F_UB), ldT<T>(in.f[F_Q11], o));
-            const float t12 = fmaf(tau, gy(F_UB), ldT<T>(in.f[F_Q12], o));
-            const float t21 = fmaf(tau, gx(F_VB), ldT<T>(in.f[F_Q21], o));
-            const float t22 = fmaf(tau, gy(F_VB), ldT<T>(in.f[F_Q22], o));
-            const float f = ball_scale_cp(fmaf(t11, t11, fmaf(t12, t12, fmaf(t21, t21, t22 * t22))));
-            y[2] = t11 * f;
-            y[3] = t12 * f;
-            y[4] = t21 * f;
-            y[5] = t22 * f;
+            float y0[6], g[6];
+            y0[0] = HAS_W ? ldT<T>(in.f[F_P1], o) : 0.f;
+            y0[1] = HAS_W ? ldT<T>(in.f[F_P2], o) : 0.f;
+            y0[2] = ldT<T>(in.f[F_Q11], o);
+            y0[3] = ldT<T>(in.f[F_Q12], o);
+            y0[4] = ldT<T>(in.f[F_Q21], o);
+            y0[5] = ldT<T>(in.f[F_Q22], o);
+            g[0] = HAS_W ? gx(F_WB) : 0.f;
+            g[1] = HAS_W ? gy(F_WB) : 0.f;
+            g[2] = gx(F_UB);
+            g[3] = gy(F_UB);
+            g[4] = gx(F_VB);
+            g[5] = gy(F_VB);
+            cp_dual<HAS_W>(y0, g, tau, y);
         };
         float y0[6], yw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, yn[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         dual(i, j, y0);
@@ -92,39 +86,24 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
         // div y^{k+1} = -K^* y^{k+1} (forward differences, Neumann)
         auto dv = [&](int cx, int cy) { return (((ex ? y0[cx] : 0.f) - yw[cx]) + (ey ? y0[cy] : 0.f)) - yn[cy]; };
         const size_t o = (size_t)i * P + j;
-        const float xw = HAS_W ? ldT<TF>(in.f[F_W], o) : 0.f;
-        const float xu = ldT<TF>(in.f[F_U], o), xv = ldT<TF>(in.f[F_V], o);
-        float zw = HAS_W ? fmaf(sg, dv(0, 1), xw) : 0.f;
-        float zu = fmaf(sg, dv(2, 3), xu), zv = fmaf(sg, dv(4, 5), xv);
-        // prox_{sigma F}: X = Z + t e with e = (beta, Ix, Iy), three cases of rho(Z) against sigma lambda |e|^2
-        const float ix = ldT<T>(Ixp, o), iy = ldT<T>(Iyp, o), it = ldT<T>(Itp, o);
-        const float e2 = fmaf(iy, iy, fmaf(ix, ix, beta * beta));
-        const float rho = fmaf(iy, zv, fmaf(ix, zu, HAS_W ? fmaf(beta, zw, it) : it));
-        const float sl = sg * lam * e2;
-        float t;
-        if (e2 <= 0.f) t = 0.f;
-        else if (rho < -sl) t = sg * lam;
-        else if (rho > sl) t = -sg * lam;
-        else t = -rho / e2;
-        if (HAS_W) zw = fmaf(t, beta, zw);
-        zu = fmaf(t, ix, zu);
-        zv = fmaf(t, iy, zv);
+        float x[3] = {HAS_W ? ldT<TF>(in.f[F_W], o) : 0.f, ldT<TF>(in.f[F_U], o), ldT<TF>(in.f[F_V], o)};
+        const float xold[3] = {x[0], x[1], x[2]};
+        const float d3[3] = {HAS_W ? dv(0, 1) : 0.f, dv(2, 3), dv(4, 5)};
+        res = cp_primal<HAS_W>(x, d3, ldT<T>(Ixp, o), ldT<T>(Iyp, o), ldT<T>(Itp, o), beta, lam, sg);
         if (HAS_W) {
             stT<T>(out.f[F_P1], o, y0[0]);
             stT<T>(out.f[F_P2], o, y0[1]);
-            stT<TF>(out.f[F_W], o, zw);
-            stT<TF>(out.f[F_WB], o, 2.f * zw - xw);
+            stT<TF>(out.f[F_W], o, x[0]);
+            stT<TF>(out.f[F_WB], o, 2.f * x[0] - xold[0]);
         }
         stT<T>(out.f[F_Q11], o, y0[2]);
         stT<T>(out.f[F_Q12], o, y0[3]);
         stT<T>(out.f[F_Q21], o, y0[4]);
         stT<T>(out.f[F_Q22], o, y0[5]);
-        stT<TF>(out.f[F_U], o, zu);
-        stT<TF>(out.f[F_V], o, zv);
-        stT<TF>(out.f[F_UB], o, 2.f * zu - xu);
-        stT<TF>(out.f[F_VB], o, 2.f * zv - xv);
-        const float dw = zw - xw, du = zu - xu, dd = zv - xv;
-        res = fmaf(dd, dd, fmaf(du, du, dw * dw));
+        stT<TF>(out.f[F_U], o, x[1]);
+        stT<TF>(out.f[F_V], o, x[2]);
+        stT<TF>(out.f[F_UB], o, 2.f * x[1] - xold[1]);
+        stT<TF>(out.f[F_VB], o, 2.f * x[2] - xold[2]);
     }
     if (A.partials) {
         const double tot = block_sum((double)res, red);

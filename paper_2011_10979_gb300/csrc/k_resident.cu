@@ -1,4 +1,4 @@
-// k_admm_resident.cu -- level-resident fused engine of the ADMM inner iteration (Sec. 3.1.1):
+// k_resident.cu -- level-resident engines of the ADMM inner iteration (Sec. 3.1.1) and of ALG1 (Sec. 4):
 // one thread-block cluster per pair keeps a whole pyramid level in shared memory and runs every
 // inner iteration of one warp (eq. rpADMMI / rpADMMII / Zach-pADMM, with the stopping test of
 // Sec. 4) in a single launch.  Coarse levels are far too small to fill the GPU, so the per-launch
@@ -34,6 +34,7 @@
 #include <type_traits>
 
 #include "k_admm_math.cuh"
+#include "k_cp_math.cuh"
 #include "tvl1_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -63,6 +64,55 @@ __device__ __forceinline__ void for_band(int npx, int W, int di, int dj, F &&f) 
         }
     }
 }
+
+// The stopping test of one cluster.  end_iteration() ends phase B of an iteration: on checking
+// (every 10th, tolerance > 0) and final iterations each CTA publishes its FP64 residual partial,
+// the cluster barrier that ends the phase follows, and every CTA sums the partials in rank order
+// (the same bits on every CTA), so the stop decision is uniform over the cluster.
+struct ClusterStop {
+    double *red;          // block-sum scratch (32 doubles, shared)
+    double *part, *total; // this CTA's partial and the broadcast total (shared)
+    double *res_check, *res_final;
+    int *done;
+    long long *iters;
+    double rows, tol;
+    int rank, nc, run = 0;
+    bool have_tot = false;
+    double last_tot = 0.0;
+
+    __device__ bool end_iteration(cg::cluster_group &cl, int it, float res, bool check, bool fin) {
+        if (check || fin) {  // uniform over the cluster
+            const double b = block_sum((double)res, red);
+            if (threadIdx.x == 0) *part = b;
+        }
+        cl.sync();
+        run = it + 1;
+        if (!(check || fin)) return false;
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int r = 0; r < nc; ++r) tot += *cl.map_shared_rank(part, r);
+            *total = tot;
+        }
+        __syncthreads();
+        last_tot = *total;
+        have_tot = true;
+        if (!check) return false;
+        if (rank == 0 && threadIdx.x == 0) *res_check = last_tot;
+        if (tol > 0.0 && sqrt(last_tot / rows) < tol) {
+            if (rank == 0 && threadIdx.x == 0) *done = 1;
+            return true;
+        }
+        return false;
+    }
+
+    // after the loop: the warp's iteration count and (last warp) the final residual
+    __device__ void finish(bool final_res) const {
+        if (rank == 0 && threadIdx.x == 0) {
+            *iters += run;
+            if (final_res && have_tot) *res_final = last_tot;
+        }
+    }
+};
 
 template <typename T, typename TF, bool HAS_W, int VARIANT>
 __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
@@ -211,9 +261,7 @@ __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
     });
     cl.sync();
 
-    int run = 0;
-    double last_tot = 0.0;
-    bool have_tot = false;
+    ClusterStop stop{red, &part, &total, res_check, res_final, donep, itersp, rows, A.tol, rank, NC};
     for (int it = 0; it < A.iters; ++it) {
         // ---- phase A: y^{k+1} (south neighbours of the last band row from the south ghost row)
         for_band(npx, W, di, dj, [&](int x, int li, int j) {
@@ -290,34 +338,9 @@ __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
             push_n(S_DQ1, li, j, dq1n);
             push_n(S_DQ2, li, j, dq2n);
         });
-        if (check || fin) {  // uniform over the cluster
-            const double b = block_sum((double)res, red);
-            if (threadIdx.x == 0) part = b;
-        }
-        cl.sync();
-        run = it + 1;
-        if (check || fin) {
-            if (threadIdx.x == 0) {
-                double tot = 0.0;
-                for (int r = 0; r < NC; ++r) tot += *cl.map_shared_rank(&part, r);
-                total = tot;
-            }
-            __syncthreads();
-            last_tot = total;
-            have_tot = true;
-            if (check) {
-                if (rank == 0 && threadIdx.x == 0) *res_check = last_tot;
-                if (A.tol > 0.0 && sqrt(last_tot / rows) < A.tol) {
-                    if (rank == 0 && threadIdx.x == 0) *donep = 1;
-                    break;  // every CTA of the cluster read the same sum: uniform
-                }
-            }
-        }
+        if (stop.end_iteration(cl, it, res, check, fin)) break;
     }
-    if (rank == 0 && threadIdx.x == 0) {
-        *itersp += run;
-        if (A.final_res && have_tot) *res_final = last_tot;
-    }
+    stop.finish(A.final_res);
 
     // ---- store the band (FP32 -> storage precision)
     for_band(npx, W, di, dj, [&](int x, int li, int j) {
@@ -332,9 +355,173 @@ __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
     cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
-template <typename T, typename TF, bool HAS_W, int VARIANT>
-cudaError_t launch_k(const ResArgs &a, int nclusters, int nc, size_t smem, cudaStream_t s) {
-    auto kern = k_admm_resident<T, TF, HAS_W, VARIANT>;
+
+// ---------------------------------------------------------------------------------- ALG1
+// The same band layout for ALG1 (Sec. 4, Chambolle-Pock): planes y (p1 p2 q11 q12 q21 q22),
+// X (w u v), Xbar (wb ub vb), data (Ix Iy It).  Phase A: y' = P(y + tau grad Xbar) (east and
+// south neighbours of Xbar; the last band row of p2, q12, q22 goes to the south CTA's north ghost
+// row).  Phase B: X' = prox(X + sigma div y') (west and north neighbours of y'), Xbar' = 2X' - X,
+// |X' - X|^2 (the first band row of Xbar' goes to the north CTA's south ghost row).  The state is
+// rounded to the storage type where the one-kernel-per-iteration engine's stores round it.
+enum { C_P1, C_P2, C_Q11, C_Q12, C_Q21, C_Q22, C_W, C_U, C_V, C_WB, C_UB, C_VB, C_IX, C_IY, C_IT };
+__constant__ int kFieldCP[12] = {F_P1, F_P2, F_Q11, F_Q12, F_Q21, F_Q22, F_W, F_U, F_V, F_WB, F_UB, F_VB};
+
+template <typename T, typename TF, bool HAS_W>
+__global__ void __launch_bounds__(RT, 1) k_cp_resident(ResArgs A) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[32];
+    __shared__ double part, total;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), NC = (int)cl.num_blocks();
+
+    int H, W, P;
+    const void *in[12], *dat[3];
+    void *out[12];
+    double *res_check, *res_final;
+    int *donep;
+    long long *itersp;
+    double rows;
+    if (A.pairs) {
+        const int q = A.list[blockIdx.x / NC];
+        const PairIter *pp = A.pairs + q;
+        const int4 gq = *reinterpret_cast<const int4 *>(&pp->g);
+        H = gq.x;
+        W = gq.y;
+        P = gq.z;
+        const Fields *fi = pp->buf + A.parity_in, *fo = pp->buf + A.parity_out;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            in[k] = fi->f[kFieldCP[k]];
+            out[k] = fo->f[kFieldCP[k]];
+        }
+        dat[0] = pp->Ix;
+        dat[1] = pp->Iy;
+        dat[2] = pp->It;
+        const PairScalars *ps = A.scal + q;
+        res_check = ps->res_check;
+        res_final = ps->res_final;
+        donep = ps->done;
+        itersp = ps->iters;
+        rows = ps->rows;
+    } else {
+        H = A.g.H;
+        W = A.g.W;
+        P = A.g.pitch;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            in[k] = A.in.f[kFieldCP[k]];
+            out[k] = A.out.f[kFieldCP[k]];
+        }
+        dat[0] = A.Ix;
+        dat[1] = A.Iy;
+        dat[2] = A.It;
+        res_check = A.sc.res_check;
+        res_final = A.sc.res_final;
+        donep = A.sc.done;
+        itersp = A.sc.iters;
+        rows = A.sc.rows;
+    }
+    const int rpc = (H + NC - 1) / NC;
+    const int r0 = rank * rpc, r1 = min(H, r0 + rpc);
+    const int nrow = max(0, r1 - r0), npx = nrow * W;
+    const int PL = (rpc + 2) * W;
+    const int di = RT / W, dj = RT - (RT / W) * W;
+    float *const S = sm + W;
+    float *const Gn = (rank > 0 && nrow > 0) ? cl.map_shared_rank(sm, rank - 1) + W + rpc * W : nullptr;
+    float *const Gs = (rank + 1 < NC && r1 < H) ? cl.map_shared_rank(sm, rank + 1) : nullptr;
+    auto push_n = [&](int k, int li, int j, float v) {
+        if (li == 0 && Gn) Gn[k * PL + j] = v;
+    };
+    auto push_s = [&](int k, int li, int j, float v) {
+        if (li == nrow - 1 && Gs) Gs[k * PL + j] = v;
+    };
+    const float tau = A.k.cp_tau, sg = A.k.cp_sigma, beta = A.k.beta, lam = A.k.lambda;
+
+    // ---- load the band; the first row of Xbar goes to the north CTA (its south ghost row)
+    for_band(npx, W, di, dj, [&](int x, int li, int j) {
+        const size_t o = (size_t)(r0 + li) * P + j;
+#pragma unroll
+        for (int k = C_P1; k <= C_Q22; ++k) S[k * PL + x] = (HAS_W || k >= C_Q11) ? ldT<T>(in[k], o) : 0.f;
+#pragma unroll
+        for (int k = C_W; k <= C_VB; ++k) {
+            const float v = (HAS_W || (k != C_W && k != C_WB)) ? ldT<TF>(in[k], o) : 0.f;
+            S[k * PL + x] = v;
+            if (k >= C_WB) push_n(k, li, j, v);
+        }
+        S[C_IX * PL + x] = ldT<T>(dat[0], o);
+        S[C_IY * PL + x] = ldT<T>(dat[1], o);
+        S[C_IT * PL + x] = ldT<T>(dat[2], o);
+    });
+    cl.sync();
+
+    ClusterStop stop{red, &part, &total, res_check, res_final, donep, itersp, rows, A.tol, rank, NC};
+    for (int it = 0; it < A.iters; ++it) {
+        // ---- phase A: y' = P(y + tau grad Xbar)
+        for_band(npx, W, di, dj, [&](int x, int li, int j) {
+            const int i = r0 + li;
+            const bool hx = j < W - 1, hy = i < H - 1;
+            auto gx = [&](int k) { return hx ? S[k * PL + x + 1] - S[k * PL + x] : 0.f; };
+            auto gy = [&](int k) { return hy ? S[k * PL + x + W] - S[k * PL + x] : 0.f; };
+            float y[6], g[6], yn[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] = (HAS_W || k >= 2) ? storage_round<T>(S[k * PL + x]) : 0.f;
+            g[0] = HAS_W ? gx(C_WB) : 0.f;
+            g[1] = HAS_W ? gy(C_WB) : 0.f;
+            g[2] = gx(C_UB);
+            g[3] = gy(C_UB);
+            g[4] = gx(C_VB);
+            g[5] = gy(C_VB);
+            cp_dual<HAS_W>(y, g, tau, yn);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) S[k * PL + x] = yn[k];
+            push_s(C_P2, li, j, yn[1]);
+            push_s(C_Q12, li, j, yn[3]);
+            push_s(C_Q22, li, j, yn[5]);
+        });
+        cl.sync();
+        // ---- phase B: X' = prox(X + sigma div y'), Xbar' = 2X' - X
+        const bool check = A.check && (it + 1) % 10 == 0;
+        const bool fin = A.final_res && it == A.iters - 1;
+        float res = 0.f;
+        for_band(npx, W, di, dj, [&](int x, int li, int j) {
+            const int i = r0 + li;
+            const bool ex = j < W - 1, ey = i < H - 1, wx = j > 0, ny = i > 0;
+            auto dv = [&](int cx, int cy) {
+                return (((ex ? S[cx * PL + x] : 0.f) - (wx ? S[cx * PL + x - 1] : 0.f)) + (ey ? S[cy * PL + x] : 0.f)) -
+                       (ny ? S[cy * PL + x - W] : 0.f);
+            };
+            float xv[3] = {HAS_W ? S[C_W * PL + x] : 0.f, S[C_U * PL + x], S[C_V * PL + x]};
+            const float xold[3] = {xv[0], xv[1], xv[2]};
+            const float d3[3] = {HAS_W ? dv(C_P1, C_P2) : 0.f, dv(C_Q11, C_Q12), dv(C_Q21, C_Q22)};
+            res += cp_primal<HAS_W>(xv, d3, S[C_IX * PL + x], S[C_IY * PL + x], S[C_IT * PL + x], beta, lam, sg);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (!HAS_W && c == 0) continue;
+                const float xb = storage_round<TF>(2.f * xv[c] - xold[c]);
+                S[(C_W + c) * PL + x] = storage_round<TF>(xv[c]);
+                S[(C_WB + c) * PL + x] = xb;
+                push_n(C_WB + c, li, j, xb);
+            }
+        });
+        if (stop.end_iteration(cl, it, res, check, fin)) break;
+    }
+    stop.finish(A.final_res);
+
+    // ---- store the band
+    for_band(npx, W, di, dj, [&](int x, int li, int j) {
+        const size_t o = (size_t)(r0 + li) * P + j;
+#pragma unroll
+        for (int k = C_P1; k <= C_Q22; ++k)
+            if (HAS_W || k >= C_Q11) stT<T>(out[k], o, S[k * PL + x]);
+#pragma unroll
+        for (int k = C_W; k <= C_VB; ++k)
+            if (HAS_W || (k != C_W && k != C_WB)) stT<TF>(out[k], o, S[k * PL + x]);
+    });
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <typename K>
+cudaError_t launch_cluster(K kern, const ResArgs &a, int nclusters, int nc, size_t smem, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (nc > 8) {
@@ -359,9 +546,10 @@ cudaError_t launch_k(const ResArgs &a, int nclusters, int nc, size_t smem, cudaS
 template <typename T, typename TF>
 cudaError_t launch_m(const ResArgs &a, int nclusters, int nc, size_t smem, cudaStream_t s) {
     const bool has_w = a.k.beta != 0.f;
-    if (a.k.method == 1)
-        return has_w ? launch_k<T, TF, true, 1>(a, nclusters, nc, smem, s) : launch_k<T, TF, false, 1>(a, nclusters, nc, smem, s);
-    return has_w ? launch_k<T, TF, true, 0>(a, nclusters, nc, smem, s) : launch_k<T, TF, false, 0>(a, nclusters, nc, smem, s);
+    auto go = [&](auto kern) { return launch_cluster(kern, a, nclusters, nc, smem, s); };
+    if (a.k.method == 3) return has_w ? go(k_cp_resident<T, TF, true>) : go(k_cp_resident<T, TF, false>);
+    if (a.k.method == 1) return has_w ? go(k_admm_resident<T, TF, true, 1>) : go(k_admm_resident<T, TF, false, 1>);
+    return has_w ? go(k_admm_resident<T, TF, true, 0>) : go(k_admm_resident<T, TF, false, 0>);
 }
 
 constexpr size_t SMEM_MAX = 200 * 1024;  // dynamic shared memory a CTA may use for its band

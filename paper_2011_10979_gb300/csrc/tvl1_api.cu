@@ -258,10 +258,10 @@ struct Batch {
 Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
 
 // Whether a level of geometry g runs its inner iterations on the level-resident engine: an ADMM
-// method, the level fits one cluster's shared memory and, with the default engine, the level is
-// small enough for the resident launch to beat one streaming kernel per iteration.
+// method or ALG1, the level fits one cluster's shared memory and, with the default engine, the
+// level is small enough for the resident launch to beat one kernel per iteration.
 bool use_resident(const of_params *p, Geom g) {
-    if (p->method == OF_PDR || p->method == OF_CP || !admm_resident_fits(g)) return false;
+    if (p->method == OF_PDR || !admm_resident_fits(g)) return false;
     return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g));
 }
 

@@ -91,7 +91,7 @@ int admm_fused_rows_per_warp(long strip_rows);   // strip_rows: sum over pairs o
 int admm_fused_strip_w();
 int admm_fused_warps();
 
-// Level-resident fused ADMM engine (k_admm_resident.cu): one thread-block cluster per pair keeps
+// Level-resident engine of the ADMM methods and ALG1 (k_resident.cu): one thread-block cluster per pair keeps
 // a whole level in shared memory and runs all inner iterations of one warp in one launch, with
 // the stopping test, the iteration count, res_check / res_final and the done flag handled inside
 // (the scalars of PairScalars).  Reads the state from `in` (buf[parity_in]) and writes the final

@@ -17,6 +17,8 @@ METHODS = {
     "rpadmm1": dict(method=0, r=1.618),
     "rpadmm2": dict(method=1, rho=1.9),
     "zach": dict(method=0, r=1.0, beta=0.0),
+    "alg1": dict(method=3),
+    "alg1_beta0": dict(method=3, beta=0.0),
 }
 FUSED, STREAM, RESIDENT = flow.OF_ENGINE_FUSED, flow.OF_ENGINE_STREAM, flow.OF_ENGINE_RESIDENT
 
@@ -59,17 +61,18 @@ def test_resident_equals_streaming(ctx, name, tol, prec, fp32_flow):
 
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 200), (200, 1), (3, 200), (17, 33), (30, 40), (120, 160),
                                  (224, 200), (1, 1000)])
-def test_resident_shapes(ctx, H, W):
+@pytest.mark.parametrize("name", ["padmm", "alg1"])
+def test_resident_shapes(ctx, H, W, name):
     """One level, shapes from a single pixel to the largest bands the shared memory holds (224 x 200:
     14 rows of 200 pixels per CTA plus two ghost rows; one row of 1000 plus ghost rows), rows fewer than the
     cluster's CTAs, single rows and columns."""
     pr = synth.random_affine_rect_pair(H, W, 11)
-    (u0, v0, s0), (u1, v1, s1) = _both(ctx, pr, lam=2.0, levels=1, warps=2, iters=25)
+    (u0, v0, s0), (u1, v1, s1) = _both(ctx, pr, lam=2.0, levels=1, warps=2, iters=25, **METHODS[name])
     assert torch.equal(u0, u1) and torch.equal(v0, v1)
     assert s0["iters_run"] == s1["iters_run"] == 50
 
 
-@pytest.mark.parametrize("name", ["padmm", "rpadmm2", "zach"])
+@pytest.mark.parametrize("name", ["padmm", "rpadmm2", "zach", "alg1"])
 def test_resident_vs_oracle_largest_band(ctx, orc, name):
     """A 224 x 200 level, 2 warps x 50 iterations, against the FP64 oracle."""
     pr = synth.random_affine_rect_pair(224, 200, 5)
@@ -85,13 +88,15 @@ def test_resident_vs_oracle_largest_band(ctx, orc, name):
 @pytest.mark.parametrize("prec", [flow.OF_PREC_FP32, flow.OF_PREC_BF16])
 @pytest.mark.parametrize("tol", [0.0, 3e-3])
 @pytest.mark.parametrize("engine", [FUSED, RESIDENT])
-def test_mixed_batch_equals_single(ctx, prec, tol, engine):
+@pytest.mark.parametrize("name", ["padmm", "alg1"])
+def test_mixed_batch_equals_single(ctx, prec, tol, engine, name):
     """A batch whose levels are resident for some pairs and streamed for others (320 x 240 is
     above the resident size) equals the single-pair solves bit for bit."""
     pairs = [synth.sinusoid_pair(seed=1), synth.random_affine_rect_pair(240, 320, 3),
              synth.random_affine_rect_pair(120, 160, 4),
              synth.Pair(np.full((1, 1), 0.5, np.float32), np.full((1, 1), 0.25, np.float32), None, None)]
-    P = flow.default_params(lam=2.0, precision=prec, tol=tol, levels=3, warps=3, iters=30, engine=engine)
+    P = flow.default_params(lam=2.0, precision=prec, tol=tol, levels=3, warps=3, iters=30, engine=engine,
+                            **METHODS[name])
     us, vs, sts = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], P)
     for p, u, v, st in zip(pairs, us, vs, sts):
         su, sv, _, sst = flow.of_solve(ctx, cu(p.I0), cu(p.I1), P)
