@@ -9,8 +9,9 @@
 // and north neighbours; each thread projects those three dual vectors itself (the neighbours'
 // own threads compute the same values), so the kernel needs no shared memory and no barrier
 // except the residual's block sum.  Residual: ||X^{k+1} - X^k||^2 (FP64 block partials).
-// Batched form: blockIdx.z selects pair pairs[z], which reads buf[parity] and writes
-// buf[parity ^ 1]; its partials occupy cp_blocks(args.g) slots from z * cp_blocks(args.g).
+// Batched form: slice z of the grid works on pair k = plist[z] (the level's pairs that are not on
+// the level-resident engine), which reads buf[parity] and writes buf[parity ^ 1]; its partials
+// occupy cp_blocks(args.g) slots from k * cp_blocks(args.g).
 #include <math.h>
 
 #include "k_cp_math.cuh"
@@ -29,8 +30,10 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
     Fields in, out;
     const void *Ixp, *Iyp, *Itp;
     const int *donep;
+    int pair = 0;
     if (A.pairs) {
-        const PairIter *pp = A.pairs + blockIdx.z;
+        pair = A.plist[blockIdx.z];
+        const PairIter *pp = A.pairs + pair;
         const int4 gq = *reinterpret_cast<const int4 *>(&pp->g);
         H = gq.x;
         W = gq.y;
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
     }
     if (A.partials) {
         const double tot = block_sum((double)res, red);
-        if (threadIdx.x == 0 && threadIdx.y == 0) A.partials[block_linear_id()] = tot;
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            A.partials[(size_t)pair * gridDim.x * gridDim.y + blockIdx.x + gridDim.x * blockIdx.y] = tot;
     }
 }
 

@@ -251,6 +251,8 @@ struct Batch {
     std::vector<char> res[MAX_LEVELS];
     int nres[MAX_LEVELS] = {};
     size_t reslist_off[MAX_LEVELS] = {}, res_smem[MAX_LEVELS] = {};
+    // the other pairs, for the one-slice-per-pair batched kernels (ALG1)
+    size_t streamlist_off[MAX_LEVELS] = {};
     size_t partials = 0, table_off = 0, table_bytes = 0, total = 0;
     std::string key;
 };
@@ -330,6 +332,8 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             t += align_up(sizeof(PairScalars) * n, 256);
             B.reslist_off[l] = t;
             t += align_up(sizeof(int) * n, 256);
+            B.streamlist_off[l] = t;
+            t += align_up(sizeof(int) * n, 256);
             const size_t np = std::max({(size_t)nt, (size_t)n * pdr_plain_blocks(gm), (size_t)n * cp_blocks(gm)});
             maxpart = std::max(maxpart, np);
         }
@@ -355,7 +359,8 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
         TileRef *tr = (TileRef *)(img.data() + B.tiles_off[l]);
         PairScalars *ps = (PairScalars *)(img.data() + B.scal_off[l]);
         int *rl = (int *)(img.data() + B.reslist_off[l]);
-        int t = 0, r = 0;
+        int *sl = (int *)(img.data() + B.streamlist_off[l]);
+        int t = 0, r = 0, ns = 0;
         const int G = cp ? cp_blocks(B.gmax[l]) : pdr_plain_blocks(B.gmax[l]);
         for (int k = 0; k < B.n; ++k) {
             const Plan &pl = B.pl[k];
@@ -385,7 +390,8 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
             const int rows = B.tile_h[l] * admm_fused_warps(), SWD = admm_fused_strip_w();
             const int t0 = t;
             if (B.res[l][k]) rl[r++] = k;
-            else
+            else sl[ns++] = k;
+            if (!B.res[l][k])
                 for (int ty = 0; ty < (g.H + rows - 1) / rows; ++ty)
                     for (int tx = 0; tx < (g.W + SWD - 1) / SWD; ++tx) tr[t++] = TileRef{k, tx, ty, 0};
             ps[k].res_check = &misc->res_check;
@@ -551,7 +557,9 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     launch_admm_resident(r, B.nres[l], B.res_smem[l], prec, pflow, s);
                 }
             }
-            const bool streamed = batched ? B.ntiles[l] > 0 || pdr || cp : !res1;
+            // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
+            // the non-resident pairs (ALG1)
+            const bool streamed = batched ? (cp ? B.nres[l] < n : (B.ntiles[l] > 0 || pdr)) : !res1;
             for (int it = 0; streamed && it < p->iters; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it == p->iters - 1;
@@ -597,7 +605,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
                         a.g = B.gmax[l];
-                        a.ntiles = n;
+                        a.ntiles = n - B.nres[l];
+                        a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
                         a.parity = (start + it) & 1;
                         launch_cp(a, prec, pflow, s);
                     } else {

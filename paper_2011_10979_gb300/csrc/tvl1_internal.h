@@ -80,6 +80,9 @@ struct IterArgs {
     const PairIter *pairs = nullptr;
     const TileRef *tiles = nullptr;
     int ntiles = 0, parity = 0, tile_h = 0;
+    // ALG1 batched form: slice z of the grid works on pair plist[z] (the pairs of the level not on
+    // the level-resident engine); its partials start at plist[z] * cp_blocks(g)
+    const int *plist = nullptr;
 };
 
 // Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w() output
