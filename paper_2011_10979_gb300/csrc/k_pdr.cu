@@ -9,6 +9,7 @@
 // plain engine the literal sequence.  Both give bitwise identical results.
 #include <math.h>
 
+#include "k_pdr_math.cuh"
 #include "tvl1_device.cuh"
 
 namespace tvl1 {
@@ -17,20 +18,25 @@ namespace {
 
 constexpr int PX = 32, PY = 8;
 
-// The planes one block works on: the single pair of the launch, or pair blockIdx.z of a batch.
+// The planes one block works on: the single pair of the launch, or in a batch the pair
+// plist[blockIdx.z] (the level's pairs not on the level-resident engine; all pairs if plist is
+// NULL).  Partial sums go to slot pair * (blocks per slice) + block within the slice.
 struct PView {
     Geom g;
     Fields f;
     const void *Ix, *Iy, *It;
     float *tmp;
     const int *done;
+    int pair;
 };
 
 __device__ __forceinline__ PView view_of(const IterArgs &A) {
     // geometry in plain scalars from one 16-byte load per mode (as in k_admm_roll.cuh)
     PView v;
+    v.pair = 0;
     if (A.pairs) {
-        const PairIter *pp = A.pairs + blockIdx.z;
+        v.pair = A.plist ? A.plist[blockIdx.z] : (int)blockIdx.z;
+        const PairIter *pp = A.pairs + v.pair;
         const int4 gq = *reinterpret_cast<const int4 *>(&pp->g);
         v.g.H = gq.x;
         v.g.W = gq.y;
@@ -58,12 +64,12 @@ __device__ __forceinline__ PView view_of(const IterArgs &A) {
 template <typename T>
 __device__ __forceinline__ float div_at(const void *a, const void *b, int i, int j, int H, int W, int P) {
     const size_t o = (size_t)i * P + j;
-    float d = 0.f;
-    if (j < W - 1) d += ldT<T>(a, o);
-    if (j > 0) d -= ldT<T>(a, o - 1);
-    if (i < H - 1) d += ldT<T>(b, o);
-    if (i > 0) d -= ldT<T>(b, o - P);
-    return d;
+    return (((j < W - 1 ? ldT<T>(a, o) : 0.f) - (j > 0 ? ldT<T>(a, o - 1) : 0.f)) + (i < H - 1 ? ldT<T>(b, o) : 0.f)) -
+           (i > 0 ? ldT<T>(b, o - P) : 0.f);
+}
+
+__device__ __forceinline__ size_t partial_slot(const PView &V) {
+    return (size_t)V.pair * gridDim.x * gridDim.y + blockIdx.x + gridDim.x * blockIdx.y;
 }
 
 // b_c = Xbar_c + sigma div ybar_c, and a copy of X^k for the residual (FP32 planes in tmp).
@@ -79,7 +85,7 @@ __global__ void k_pdr_b(IterArgs A, bool has_w) {
     const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
     const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
     for (int c = has_w ? 0 : 1; c < 3; ++c) {
-        tmp[c * plane + o] = ldT<TF>(V.f.f[XB[c]], o) + A.k.sigma * div_at<T>(V.f.f[Y1[c]], V.f.f[Y2[c]], i, j, H, W, P);
+        tmp[c * plane + o] = pdr_rhs(ldT<TF>(V.f.f[XB[c]], o), div_at<T>(V.f.f[Y1[c]], V.f.f[Y2[c]], i, j, H, W, P), A.k.sigma);
         tmp[(3 + c) * plane + o] = ldT<TF>(V.f.f[X[c]], o);
     }
 }
@@ -104,7 +110,7 @@ __global__ void k_gs_half(IterArgs A, int colour, bool has_w) {
         if (j < W - 1) { acc += ldT<TF>(x, o + 1); ++nb; }
         if (i > 0) { acc += ldT<TF>(x, o - P); ++nb; }
         if (i < H - 1) { acc += ldT<TF>(x, o + P); ++nb; }
-        stT<TF>(V.f.f[X[c]], o, (tmp[c * plane + o] + st * acc) / (1.f + st * (float)nb));
+        stT<TF>(V.f.f[X[c]], o, pdr_gs(tmp[c * plane + o], acc, nb, st));
     }
 }
 
@@ -122,49 +128,39 @@ __global__ void k_pdr_finish(IterArgs A, bool has_w) {
         const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
         const float beta = A.k.beta, lam = A.k.lambda, sg = A.k.sigma, ta = A.k.tau;
         const float ix = ldT<T>(V.Ix, o), iy = ldT<T>(V.Iy, o), it = ldT<T>(V.It, o);
-        const float xw = has_w ? ldT<TF>(V.f.f[F_W], o) : 0.f;
-        const float xu = ldT<TF>(V.f.f[F_U], o), xv = ldT<TF>(V.f.f[F_V], o);
-        const float bw = has_w ? ldT<TF>(V.f.f[F_WB], o) : 0.f;
-        const float bu = ldT<TF>(V.f.f[F_UB], o), bv = ldT<TF>(V.f.f[F_VB], o);
-        float zw = has_w ? 2.f * xw - bw : 0.f, zu = 2.f * xu - bu, zv = 2.f * xv - bv;
-        const float e2 = beta * beta + ix * ix + iy * iy;
-        const float rho = it + beta * zw + ix * zu + iy * zv;
-        float t;
-        if (e2 <= 0.f) t = 0.f;
-        else if (rho < -sg * lam * e2) t = sg * lam;
-        else if (rho > sg * lam * e2) t = -sg * lam;
-        else t = -rho / e2;
-        zw += t * beta;
-        zu += t * ix;
-        zv += t * iy;
-        if (has_w) stT<TF>(V.f.f[F_WB], o, bw + zw - xw);
-        stT<TF>(V.f.f[F_UB], o, bu + zu - xu);
-        stT<TF>(V.f.f[F_VB], o, bv + zv - xv);
+        const float x[3] = {has_w ? ldT<TF>(V.f.f[F_W], o) : 0.f, ldT<TF>(V.f.f[F_U], o), ldT<TF>(V.f.f[F_V], o)};
+        float xb[3] = {has_w ? ldT<TF>(V.f.f[F_WB], o) : 0.f, ldT<TF>(V.f.f[F_UB], o), ldT<TF>(V.f.f[F_VB], o)};
+        if (has_w) pdr_xbar<true>(x, xb, ix, iy, it, beta, lam, sg);
+        else pdr_xbar<false>(x, xb, ix, iy, it, beta, lam, sg);
+        if (has_w) stT<TF>(V.f.f[F_WB], o, xb[0]);
+        stT<TF>(V.f.f[F_UB], o, xb[1]);
+        stT<TF>(V.f.f[F_VB], o, xb[2]);
         const bool hx = j < W - 1, hy = i < H - 1;
         auto gx = [&](int f, float x0) { return hx ? ldT<TF>(V.f.f[f], o + 1) - x0 : 0.f; };
         auto gy = [&](int f, float x0) { return hy ? ldT<TF>(V.f.f[f], o + P) - x0 : 0.f; };
+        const float g[6] = {has_w ? gx(F_W, x[0]) : 0.f, has_w ? gy(F_W, x[0]) : 0.f, gx(F_U, x[1]), gy(F_U, x[1]),
+                            gx(F_V, x[2]), gy(F_V, x[2])};
+        const float y[6] = {has_w ? ldT<T>(V.f.f[F_P1], o) : 0.f, has_w ? ldT<T>(V.f.f[F_P2], o) : 0.f,
+                            ldT<T>(V.f.f[F_Q11], o), ldT<T>(V.f.f[F_Q12], o), ldT<T>(V.f.f[F_Q21], o),
+                            ldT<T>(V.f.f[F_Q22], o)};
+        float yn[6];
+        if (has_w) pdr_ybar<true>(y, g, ta, yn);
+        else pdr_ybar<false>(y, g, ta, yn);
         if (has_w) {
-            const float g1 = gx(F_W, xw), g2 = gy(F_W, xw);
-            const float t1 = ldT<T>(V.f.f[F_P1], o) + 2.f * ta * g1, t2 = ldT<T>(V.f.f[F_P2], o) + 2.f * ta * g2;
-            const float f = fmaxf(1.f, sqrtf(t1 * t1 + t2 * t2));
-            stT<T>(V.f.f[F_P1], o, t1 / f - ta * g1);
-            stT<T>(V.f.f[F_P2], o, t2 / f - ta * g2);
+            stT<T>(V.f.f[F_P1], o, yn[0]);
+            stT<T>(V.f.f[F_P2], o, yn[1]);
         }
-        const float ux = gx(F_U, xu), uy = gy(F_U, xu), vx = gx(F_V, xv), vy = gy(F_V, xv);
-        const float t11 = ldT<T>(V.f.f[F_Q11], o) + 2.f * ta * ux, t12 = ldT<T>(V.f.f[F_Q12], o) + 2.f * ta * uy;
-        const float t21 = ldT<T>(V.f.f[F_Q21], o) + 2.f * ta * vx, t22 = ldT<T>(V.f.f[F_Q22], o) + 2.f * ta * vy;
-        const float f = fmaxf(1.f, sqrtf(t11 * t11 + t12 * t12 + t21 * t21 + t22 * t22));
-        stT<T>(V.f.f[F_Q11], o, t11 / f - ta * ux);
-        stT<T>(V.f.f[F_Q12], o, t12 / f - ta * uy);
-        stT<T>(V.f.f[F_Q21], o, t21 / f - ta * vx);
-        stT<T>(V.f.f[F_Q22], o, t22 / f - ta * vy);
-        const float dw = has_w ? xw - tmp[3 * plane + o] : 0.f;
-        const float du = xu - tmp[4 * plane + o], dv = xv - tmp[5 * plane + o];
+        stT<T>(V.f.f[F_Q11], o, yn[2]);
+        stT<T>(V.f.f[F_Q12], o, yn[3]);
+        stT<T>(V.f.f[F_Q21], o, yn[4]);
+        stT<T>(V.f.f[F_Q22], o, yn[5]);
+        const float dw = has_w ? x[0] - tmp[3 * plane + o] : 0.f;
+        const float du = x[1] - tmp[4 * plane + o], dv = x[2] - tmp[5 * plane + o];
         res = (double)dw * dw + (double)du * du + (double)dv * dv;
     }
     if (A.partials) {
         const double tot = block_sum(res, red);
-        if (threadIdx.x == 0 && threadIdx.y == 0) A.partials[block_linear_id()] = tot;
+        if (threadIdx.x == 0 && threadIdx.y == 0) A.partials[partial_slot(V)] = tot;
     }
 }
 

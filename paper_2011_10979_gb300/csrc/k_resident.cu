@@ -35,6 +35,7 @@
 
 #include "k_admm_math.cuh"
 #include "k_cp_math.cuh"
+#include "k_pdr_math.cuh"
 #include "tvl1_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -520,6 +521,216 @@ __global__ void __launch_bounds__(RT, 1) k_cp_resident(ResArgs A) {
     cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
+// ---------------------------------------------------------------------------------- pDR
+// The band layout for pDR (Sec. 3.1.2): planes X (w u v), Xbar, ybar (p1 p2 q11 q12 q21 q22), the
+// data, the right-hand side b and X^k (for the residual): 21 planes.  Per iteration:
+//   1. b = Xbar + sigma div ybar and X^k at every band pixel, then the red Gauss-Seidel update at
+//      the red ones (it reads only its own b and black neighbours, which this phase leaves alone);
+//   2. n times: black half-sweep, red half-sweep (the fused engine's R (B R)^n);
+//   3. Xbar and ybar updates (east and south neighbours of X^{k+1}) and |X^{k+1} - X^k|^2.
+// Each half-sweep writes the updated pixels of the first / last band row into the neighbours'
+// ghost rows; within a half-sweep a CTA reads only the other colour of its ghost rows, which no
+// CTA writes in that half-sweep.  The last band row of ybar goes to the south CTA after step 3.
+// The state is rounded to the storage type where the per-kernel engine's stores round it.
+enum { D_W, D_U, D_V, D_WB, D_UB, D_VB, D_P1, D_P2, D_Q11, D_Q12, D_Q21, D_Q22, D_IX, D_IY, D_IT, D_B, D_O = D_B + 3 };
+constexpr int NPL_PDR = D_O + 3;
+__constant__ int kFieldPDR[12] = {F_W, F_U, F_V, F_WB, F_UB, F_VB, F_P1, F_P2, F_Q11, F_Q12, F_Q21, F_Q22};
+
+template <typename T, typename TF, bool HAS_W>
+__global__ void __launch_bounds__(RT, 1) k_pdr_resident(ResArgs A) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[32];
+    __shared__ double part, total;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), NC = (int)cl.num_blocks();
+
+    int H, W, P;
+    const void *in[12], *dat[3];
+    void *out[12];
+    double *res_check, *res_final;
+    int *donep;
+    long long *itersp;
+    double rows;
+    if (A.pairs) {
+        const int q = A.list[blockIdx.x / NC];
+        const PairIter *pp = A.pairs + q;
+        const int4 gq = *reinterpret_cast<const int4 *>(&pp->g);
+        H = gq.x;
+        W = gq.y;
+        P = gq.z;
+        const Fields *fi = pp->buf + A.parity_in, *fo = pp->buf + A.parity_out;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            in[k] = fi->f[kFieldPDR[k]];
+            out[k] = fo->f[kFieldPDR[k]];
+        }
+        dat[0] = pp->Ix;
+        dat[1] = pp->Iy;
+        dat[2] = pp->It;
+        const PairScalars *ps = A.scal + q;
+        res_check = ps->res_check;
+        res_final = ps->res_final;
+        donep = ps->done;
+        itersp = ps->iters;
+        rows = ps->rows;
+    } else {
+        H = A.g.H;
+        W = A.g.W;
+        P = A.g.pitch;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            in[k] = A.in.f[kFieldPDR[k]];
+            out[k] = A.out.f[kFieldPDR[k]];
+        }
+        dat[0] = A.Ix;
+        dat[1] = A.Iy;
+        dat[2] = A.It;
+        res_check = A.sc.res_check;
+        res_final = A.sc.res_final;
+        donep = A.sc.done;
+        itersp = A.sc.iters;
+        rows = A.sc.rows;
+    }
+    const int rpc = (H + NC - 1) / NC;
+    const int r0 = rank * rpc, r1 = min(H, r0 + rpc);
+    const int nrow = max(0, r1 - r0), npx = nrow * W;
+    const int PL = (rpc + 2) * W;
+    const int di = RT / W, dj = RT - (RT / W) * W;
+    float *const S = sm + W;
+    float *const Gn = (rank > 0 && nrow > 0) ? cl.map_shared_rank(sm, rank - 1) + W + rpc * W : nullptr;
+    float *const Gs = (rank + 1 < NC && r1 < H) ? cl.map_shared_rank(sm, rank + 1) : nullptr;
+    auto push_n = [&](int k, int li, int j, float v) {
+        if (li == 0 && Gn) Gn[k * PL + j] = v;
+    };
+    auto push_s = [&](int k, int li, int j, float v) {
+        if (li == nrow - 1 && Gs) Gs[k * PL + j] = v;
+    };
+    const float sg = A.k.sigma, ta = A.k.tau, st = A.k.sigma * A.k.tau, beta = A.k.beta, lam = A.k.lambda;
+    const int c0 = HAS_W ? 0 : 1;
+
+    // ---- load the band; boundary rows of X to both neighbours, the last row of ybar to the south
+    for_band(npx, W, di, dj, [&](int x, int li, int j) {
+        const size_t o = (size_t)(r0 + li) * P + j;
+#pragma unroll
+        for (int k = D_W; k <= D_VB; ++k) {
+            const float v = (HAS_W || (k != D_W && k != D_WB)) ? ldT<TF>(in[k], o) : 0.f;
+            S[k * PL + x] = v;
+            if (k <= D_V) {
+                push_n(k, li, j, v);
+                push_s(k, li, j, v);
+            }
+        }
+#pragma unroll
+        for (int k = D_P1; k <= D_Q22; ++k) {
+            const float v = (HAS_W || k >= D_Q11) ? ldT<T>(in[k], o) : 0.f;
+            S[k * PL + x] = v;
+            if (k == D_P2 || k == D_Q12 || k == D_Q22) push_s(k, li, j, v);
+        }
+        S[D_IX * PL + x] = ldT<T>(dat[0], o);
+        S[D_IY * PL + x] = ldT<T>(dat[1], o);
+        S[D_IT * PL + x] = ldT<T>(dat[2], o);
+    });
+    cl.sync();
+
+    // one Gauss-Seidel update of the pixel's X (all components), stored rounded and pushed
+    auto gs_pixel = [&](int x, int li, int j) {
+        const int i = r0 + li;
+        const bool hw = j > 0, he = j < W - 1, hn = i > 0, hs = i < H - 1;
+        const int nb = (int)hw + (int)he + (int)hn + (int)hs;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c < c0) continue;
+            const float *Xc = S + (D_W + c) * PL;
+            float acc = 0.f;
+            if (hw) acc += Xc[x - 1];
+            if (he) acc += Xc[x + 1];
+            if (hn) acc += Xc[x - W];
+            if (hs) acc += Xc[x + W];
+            const float v = storage_round<TF>(pdr_gs(S[(D_B + c) * PL + x], acc, nb, st));
+            S[(D_W + c) * PL + x] = v;
+            push_n(D_W + c, li, j, v);
+            push_s(D_W + c, li, j, v);
+        }
+    };
+    ClusterStop stop{red, &part, &total, res_check, res_final, donep, itersp, rows, A.tol, rank, NC};
+    for (int it = 0; it < A.iters; ++it) {
+        // ---- 1. b = Xbar + sigma div ybar, X^k, and the red half-sweep
+        for_band(npx, W, di, dj, [&](int x, int li, int j) {
+            const int i = r0 + li;
+            const bool ex = j < W - 1, wx = j > 0, ey = i < H - 1, ny = i > 0;
+            const int Y1[3] = {D_P1, D_Q11, D_Q21}, Y2[3] = {D_P2, D_Q12, D_Q22};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (c < c0) continue;
+                const float *a = S + Y1[c] * PL, *b = S + Y2[c] * PL;
+                const float dv = (((ex ? a[x] : 0.f) - (wx ? a[x - 1] : 0.f)) + (ey ? b[x] : 0.f)) - (ny ? b[x - W] : 0.f);
+                S[(D_B + c) * PL + x] = pdr_rhs(S[(D_WB + c) * PL + x], dv, sg);
+                S[(D_O + c) * PL + x] = S[(D_W + c) * PL + x];
+            }
+            if (((i + j) & 1) == 0) gs_pixel(x, li, j);
+        });
+        cl.sync();
+        // ---- 2. (black, red)^n
+        for (int sw = 0; sw < A.k.gs_sweeps; ++sw) {
+            for (int colour = 1; colour >= 0; --colour) {
+                for_band(npx, W, di, dj, [&](int x, int li, int j) {
+                    if (((r0 + li + j) & 1) == colour) gs_pixel(x, li, j);
+                });
+                cl.sync();
+            }
+        }
+        // ---- 3. Xbar, ybar, residual
+        const bool check = A.check && (it + 1) % 10 == 0;
+        const bool fin = A.final_res && it == A.iters - 1;
+        float res = 0.f;
+        for_band(npx, W, di, dj, [&](int x, int li, int j) {
+            const int i = r0 + li;
+            const bool hx = j < W - 1, hy = i < H - 1;
+            const float xv[3] = {HAS_W ? S[D_W * PL + x] : 0.f, S[D_U * PL + x], S[D_V * PL + x]};
+            float xb[3] = {HAS_W ? S[D_WB * PL + x] : 0.f, S[D_UB * PL + x], S[D_VB * PL + x]};
+            pdr_xbar<HAS_W>(xv, xb, S[D_IX * PL + x], S[D_IY * PL + x], S[D_IT * PL + x], beta, lam, sg);
+            float g[6], y[6], yn[6];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float *Xc = S + (D_W + c) * PL;
+                g[2 * c] = (HAS_W || c > 0) && hx ? Xc[x + 1] - xv[c] : 0.f;
+                g[2 * c + 1] = (HAS_W || c > 0) && hy ? Xc[x + W] - xv[c] : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) y[k] = (HAS_W || k >= 2) ? S[(D_P1 + k) * PL + x] : 0.f;
+            pdr_ybar<HAS_W>(y, g, ta, yn);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (c < c0) continue;
+                S[(D_WB + c) * PL + x] = storage_round<TF>(xb[c]);
+                const float d = xv[c] - S[(D_O + c) * PL + x];
+                res = fmaf(d, d, res);
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                if (!HAS_W && k < 2) continue;
+                const float v = storage_round<T>(yn[k]);
+                S[(D_P1 + k) * PL + x] = v;
+                if (k == 1 || k == 3 || k == 5) push_s(D_P1 + k, li, j, v);
+            }
+        });
+        if (stop.end_iteration(cl, it, res, check, fin)) break;
+    }
+    stop.finish(A.final_res);
+
+    // ---- store the band
+    for_band(npx, W, di, dj, [&](int x, int li, int j) {
+        const size_t o = (size_t)(r0 + li) * P + j;
+#pragma unroll
+        for (int k = D_W; k <= D_VB; ++k)
+            if (HAS_W || (k != D_W && k != D_WB)) stT<TF>(out[k], o, S[k * PL + x]);
+#pragma unroll
+        for (int k = D_P1; k <= D_Q22; ++k)
+            if (HAS_W || k >= D_Q11) stT<T>(out[k], o, S[k * PL + x]);
+    });
+    cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
 template <typename K>
 cudaError_t launch_cluster(K kern, const ResArgs &a, int nclusters, int nc, size_t smem, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -548,6 +759,7 @@ cudaError_t launch_m(const ResArgs &a, int nclusters, int nc, size_t smem, cudaS
     const bool has_w = a.k.beta != 0.f;
     auto go = [&](auto kern) { return launch_cluster(kern, a, nclusters, nc, smem, s); };
     if (a.k.method == 3) return has_w ? go(k_cp_resident<T, TF, true>) : go(k_cp_resident<T, TF, false>);
+    if (a.k.method == 2) return has_w ? go(k_pdr_resident<T, TF, true>) : go(k_pdr_resident<T, TF, false>);
     if (a.k.method == 1) return has_w ? go(k_admm_resident<T, TF, true, 1>) : go(k_admm_resident<T, TF, false, 1>);
     return has_w ? go(k_admm_resident<T, TF, true, 0>) : go(k_admm_resident<T, TF, false, 0>);
 }
@@ -607,15 +819,19 @@ int admm_resident_max_clusters() {
     return m;
 }
 
-size_t admm_resident_smem(Geom g) {
+size_t admm_resident_smem(Geom g, int method) {
     const int nc = admm_resident_cluster();
     const size_t rpc = (size_t)((g.H + nc - 1) / nc);
-    return (rpc + 2) * (size_t)g.W * NPL * sizeof(float);
+    return (rpc + 2) * (size_t)g.W * (method == 2 ? NPL_PDR : NPL) * sizeof(float);
 }
 
-bool admm_resident_fits(Geom g) { return g.H >= 1 && g.W >= 1 && admm_resident_smem(g) <= SMEM_MAX; }
+bool admm_resident_fits(Geom g, int method) {
+    return g.H >= 1 && g.W >= 1 && admm_resident_smem(g, method) <= SMEM_MAX;
+}
 
-bool admm_resident_preferred(Geom g) { return (long)g.H * g.W <= RESIDENT_MAX_PX; }
+// pDR's per-kernel engine takes 2n + 3 launches per iteration, so its resident form wins at every
+// size that fits; the ADMM methods and ALG1 (one launch per iteration) only up to RESIDENT_MAX_PX.
+bool admm_resident_preferred(Geom g, int method) { return method == 2 || (long)g.H * g.W <= RESIDENT_MAX_PX; }
 
 cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, size_t smem, int prec, int prec_flow,
                                  cudaStream_t s) {

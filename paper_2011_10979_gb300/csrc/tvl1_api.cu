@@ -259,12 +259,12 @@ struct Batch {
 
 Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
 
-// Whether a level of geometry g runs its inner iterations on the level-resident engine: an ADMM
-// method or ALG1, the level fits one cluster's shared memory and, with the default engine, the
-// level is small enough for the resident launch to beat one kernel per iteration.
+// Whether a level of geometry g runs its inner iterations on the level-resident engine: the level
+// fits one cluster's shared memory and, with the default engine, is small enough for the resident
+// launch to beat the per-iteration kernels (all methods have a resident form).
 bool use_resident(const of_params *p, Geom g) {
-    if (p->method == OF_PDR || !admm_resident_fits(g)) return false;
-    return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g));
+    if (!admm_resident_fits(g, p->method)) return false;
+    return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g, p->method));
 }
 
 Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
@@ -306,7 +306,7 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
                 if (take && use_resident(p, g)) {
                     B.res[l][k] = 1;
                     ++B.nres[l];
-                    B.res_smem[l] = std::max(B.res_smem[l], admm_resident_smem(g));
+                    B.res_smem[l] = std::max(B.res_smem[l], admm_resident_smem(g, p->method));
                     continue;
                 }
                 strip_rows += (long)((g.W + SWD - 1) / SWD) * g.H;
@@ -530,7 +530,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 r.final_res = last_warp;
                 r.tol = p->tol;
                 r.parity_in = start;
-                r.parity_out = (start + p->iters) & 1;
+                r.parity_out = pingpong ? (start + p->iters) & 1 : start;  // pDR works in place
                 if (res1) {
                     const PairCtx &c = pc[0];
                     const Geom g = geom_of(*c.pl, l);
@@ -549,7 +549,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     r.sc.iters = &c.misc->iters;
                     r.sc.rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
                     r.sc.resident = 1;
-                    launch_admm_resident(r, 1, admm_resident_smem(g), prec, pflow, s);
+                    launch_admm_resident(r, 1, admm_resident_smem(g, p->method), prec, pflow, s);
                 } else {
                     r.pairs = (const PairIter *)(ctx->arena + B.table_off + B.pairs_off[l][in32 ? 1 : 0]);
                     r.scal = (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]);
@@ -559,7 +559,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             }
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
             // the non-resident pairs (ALG1)
-            const bool streamed = batched ? (cp ? B.nres[l] < n : (B.ntiles[l] > 0 || pdr)) : !res1;
+            const bool streamed = batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1;
             for (int it = 0; streamed && it < p->iters; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it == p->iters - 1;
@@ -600,7 +600,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     a.partials = (check || final_it) ? bpart : nullptr;
                     if (pdr) {
                         a.g = B.gmax[l];
-                        a.ntiles = n;
+                        a.ntiles = n - B.nres[l];
+                        a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
                         a.parity = start;
                         launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {

@@ -94,7 +94,7 @@ int admm_fused_rows_per_warp(long strip_rows);   // strip_rows: sum over pairs o
 int admm_fused_strip_w();
 int admm_fused_warps();
 
-// Level-resident engine of the ADMM methods and ALG1 (k_resident.cu): one thread-block cluster per pair keeps
+// Level-resident engine of the ADMM methods, pDR and ALG1 (k_resident.cu): one thread-block cluster per pair keeps
 // a whole level in shared memory and runs all inner iterations of one warp in one launch, with
 // the stopping test, the iteration count, res_check / res_final and the done flag handled inside
 // (the scalars of PairScalars).  Reads the state from `in` (buf[parity_in]) and writes the final
@@ -117,9 +117,9 @@ struct ResArgs {
 };
 int admm_resident_cluster();           // CTAs per cluster: 16 where the device schedules it, else 8
 int admm_resident_max_clusters();      // resident clusters that run at once (one CTA per SM)
-size_t admm_resident_smem(Geom g);     // dynamic shared memory of one CTA for this level
-bool admm_resident_fits(Geom g);       // whether a level of this geometry fits one cluster
-bool admm_resident_preferred(Geom g);  // whether the resident launch is the faster engine for it
+size_t admm_resident_smem(Geom g, int method);  // dynamic shared memory of one CTA for this level
+bool admm_resident_fits(Geom g, int method);    // whether a level of this geometry fits one cluster
+bool admm_resident_preferred(Geom g, int method);  // whether the resident launch is the faster engine
 cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, size_t smem, int prec, int prec_flow,
                                  cudaStream_t s);
 

@@ -19,6 +19,8 @@ METHODS = {
     "zach": dict(method=0, r=1.0, beta=0.0),
     "alg1": dict(method=3),
     "alg1_beta0": dict(method=3, beta=0.0),
+    "pdr": dict(method=2),
+    "pdr_beta0_2sweeps": dict(method=2, beta=0.0, gs_sweeps=2),
 }
 FUSED, STREAM, RESIDENT = flow.OF_ENGINE_FUSED, flow.OF_ENGINE_STREAM, flow.OF_ENGINE_RESIDENT
 
@@ -61,7 +63,7 @@ def test_resident_equals_streaming(ctx, name, tol, prec, fp32_flow):
 
 @pytest.mark.parametrize("H,W", [(1, 1), (1, 200), (200, 1), (3, 200), (17, 33), (30, 40), (120, 160),
                                  (224, 200), (1, 1000)])
-@pytest.mark.parametrize("name", ["padmm", "alg1"])
+@pytest.mark.parametrize("name", ["padmm", "alg1", "pdr"])
 def test_resident_shapes(ctx, H, W, name):
     """One level, shapes from a single pixel to the largest bands the shared memory holds (224 x 200:
     14 rows of 200 pixels per CTA plus two ghost rows; one row of 1000 plus ghost rows), rows fewer than the
@@ -72,10 +74,12 @@ def test_resident_shapes(ctx, H, W, name):
     assert s0["iters_run"] == s1["iters_run"] == 50
 
 
-@pytest.mark.parametrize("name", ["padmm", "rpadmm2", "zach", "alg1"])
+@pytest.mark.parametrize("name", ["padmm", "rpadmm2", "zach", "alg1", "pdr"])
 def test_resident_vs_oracle_largest_band(ctx, orc, name):
-    """A 224 x 200 level, 2 warps x 50 iterations, against the FP64 oracle."""
-    pr = synth.random_affine_rect_pair(224, 200, 5)
+    """The largest level the cluster's shared memory holds (224 x 200; pDR, with 21 planes per
+    pixel, 150 x 150), 2 warps x 50 iterations, against the FP64 oracle."""
+    H, W = (150, 150) if name == "pdr" else (224, 200)
+    pr = synth.random_affine_rect_pair(H, W, 5)
     kw = dict(lam=5.0, levels=1, warps=2, iters=50, **METHODS[name])
     u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), flow.default_params(engine=RESIDENT, **kw))
     ru, rv, _, rst = orc.solve(pr.I0, pr.I1, orc.Params(**kw))
@@ -88,7 +92,7 @@ def test_resident_vs_oracle_largest_band(ctx, orc, name):
 @pytest.mark.parametrize("prec", [flow.OF_PREC_FP32, flow.OF_PREC_BF16])
 @pytest.mark.parametrize("tol", [0.0, 3e-3])
 @pytest.mark.parametrize("engine", [FUSED, RESIDENT])
-@pytest.mark.parametrize("name", ["padmm", "alg1"])
+@pytest.mark.parametrize("name", ["padmm", "alg1", "pdr"])
 def test_mixed_batch_equals_single(ctx, prec, tol, engine, name):
     """A batch whose levels are resident for some pairs and streamed for others (320 x 240 is
     above the resident size) equals the single-pair solves bit for bit."""
