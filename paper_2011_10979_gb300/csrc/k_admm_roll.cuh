@@ -180,9 +180,6 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TY>
 __global__ void __launch_bounds__(WARPS * 32) k_admm_roll(IterArgs A) {
     __shared__ double red[32];
-    // programmatic dependent launch: the next iteration's grid may start launching once every
-    // block of this one runs; it waits (griddepcontrol.wait below) before touching the state
-    asm volatile("griddepcontrol.launch_dependents;");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // ---- which strip: geometry in plain scalars, one 16-byte load per mode
     int H, W, P, sx, sy;
@@ -229,9 +226,6 @@ __global__ void __launch_bounds__(WARPS * 32) k_admm_roll(IterArgs A) {
             src[9] = A.It;
         }
     }
-    // everything above reads only launch parameters and the static work-list tables; from here on
-    // the kernel reads what earlier kernels wrote, so wait until they have completed
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int stopped = donep ? *donep : 0;
     const float at = a_tilde_of(A.k, msp);
     if (stopped) return;  // uniform per block: the pair's warp met its stopping test
@@ -249,16 +243,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_admm_roll(IterArgs A) {
 }
 
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TY> void launch_t(const IterArgs &a, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = a.tiles ? dim3(a.ntiles) : dim3((a.g.W + SW - 1) / SW, (a.g.H + TY * WARPS - 1) / (TY * WARPS));
-    cfg.blockDim = dim3(32 * WARPS);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_admm_roll<T, TF, HAS_W, VARIANT, TY>, a);
+    dim3 grid = a.tiles ? dim3(a.ntiles)
+                        : dim3((a.g.W + SW - 1) / SW, (a.g.H + TY * WARPS - 1) / (TY * WARPS));
+    k_admm_roll<T, TF, HAS_W, VARIANT, TY><<<grid, dim3(32 * WARPS), 0, s>>>(a);
 }
 
 template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_ty(const IterArgs &a, int ty, cudaStream_t s) {
