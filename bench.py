@@ -211,29 +211,32 @@ def run_ours(args):
     t_e2e = (time.perf_counter() - t0) / n_e2e
     t_step, t_e2e = reduce_max_over_ranks([t_step, t_e2e], dev)
     # dominant kernel: the streaming pADMM iteration at the finest level, timed inside the solve graph
-    roof = kernel_roofline(flow, torch, dev, pr)
     launches = flow.of_solve_kernel_count(ctx, H, W, P)
-    # plain single-pair FP32 GPU path (one kernel per operator), same workload
-    Pp = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
-                             engine=flow.OF_ENGINE_PLAIN)
-    flow.of_solve(ctx, I0, I1, Pp, stats=False)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(3):
+    full = args.legs == "all"
+    roof = kernel_roofline(flow, torch, dev, pr) if full else None
+    t_plain = serving = batch = batch_all16 = prec_line = solvers = None
+    if full:
+        # plain single-pair FP32 GPU path (one kernel per operator), same workload
+        Pp = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
+                                 engine=flow.OF_ENGINE_PLAIN)
         flow.of_solve(ctx, I0, I1, Pp, stats=False)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_plain = e0.elapsed_time(e1) / 3 / 1e3
-    serving = serving_measure(flow, torch, dev)
-    batch = batch_measure(flow, torch, dev, fp32_flow=1)
-    batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
-    prec_line = precision_measure(flow, torch, dev)
-    solvers = solvers_measure(flow, torch, dev, I0, I1, pr)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            flow.of_solve(ctx, I0, I1, Pp, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_plain = e0.elapsed_time(e1) / 3 / 1e3
+        serving = serving_measure(flow, torch, dev)
+        batch = batch_measure(flow, torch, dev, fp32_flow=1)
+        batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
+        prec_line = precision_measure(flow, torch, dev)
+        solvers = solvers_measure(flow, torch, dev, I0, I1, pr)
     if rank != 0:
         return
     cpu = None
-    if ws == 1:
+    if ws == 1 and full:
         rate, dt, desc, (ou, ov) = cpu_oracle_rate()
         # accuracy of the timed path on the sampled levels
         Ps = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
@@ -253,7 +256,7 @@ def run_ours(args):
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if ws > 1 else "single"},
             "mpix_iter_per_s": work * ws / t_step,
             "plain_gpu": {"value": 1.0 / t_plain, "unit": "flows/s", "engine": "plain (one kernel per operator)",
-                          "speedup": t_plain / t_step},
+                          "speedup": t_plain / t_step} if full else None,
             "roofline": roof,
             "batch": batch,
             "serving": serving,
@@ -265,6 +268,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": 2 * H * W * 4},
             "gpu_launches": int(launches) * args.steps,
             "clocks": clocks}
+    if not full:
+        line["legs"] = args.legs
     print(json.dumps(line), flush=True)
 
 
@@ -497,6 +502,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    # "solve": only the timed single-pair solve (and its e2e leg), e.g. as a short command to run
+    # under a profiler; "all" (default) adds the roofline, plain, batch, serving, precision, solver
+    # and CPU-baseline legs
+    ap.add_argument("--legs", default="all", choices=["all", "solve"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
