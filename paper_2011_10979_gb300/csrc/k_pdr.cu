@@ -6,7 +6,9 @@
 // A red-black Gauss-Seidel half-sweep updates one colour from the other colour's values only, so
 // it is data-parallel and in place.  One symmetric sweep is red, black, black, red; the repeated
 // black half-sweep recomputes identical values, so the fused engine runs red (black red)^n, the
-// plain engine the literal sequence.  Both give bitwise identical results.
+// plain engine the literal sequence.  Both give bitwise identical results.  The fused engine takes
+// 2n + 1 launches per iteration: the right-hand side with the first red half-sweep, the half-sweeps
+// between, and the last red half-sweep with the Xbar / ybar updates.
 #include <math.h>
 
 #include "k_pdr_math.cuh"
@@ -90,6 +92,111 @@ __global__ void k_pdr_b(IterArgs A, bool has_w) {
     }
 }
 
+// The Gauss-Seidel update of component c at pixel (a, b) from b (tmp plane c) and the current X of
+// its in-domain neighbours (west, east, north, south), rounded to the flow storage type as a store
+// and a load would round it.
+template <typename TF>
+__device__ __forceinline__ float gs_value(const PView &V, const float *tmp, size_t plane, int c, int a, int b,
+                                          float st) {
+    const int H = V.g.H, W = V.g.W, P = V.g.pitch;
+    const int X[3] = {F_W, F_U, F_V};
+    const void *x = V.f.f[X[c]];
+    const size_t o = (size_t)a * P + b;
+    float acc = 0.f;
+    int nb = 0;
+    if (b > 0) { acc += ldT<TF>(x, o - 1); ++nb; }
+    if (b < W - 1) { acc += ldT<TF>(x, o + 1); ++nb; }
+    if (a > 0) { acc += ldT<TF>(x, o - P); ++nb; }
+    if (a < H - 1) { acc += ldT<TF>(x, o + P); ++nb; }
+    return storage_round<TF>(pdr_gs(tmp[c * plane + o], acc, nb, st));
+}
+
+// Fused engine, first kernel of an iteration: b = Xbar + sigma div ybar and X^k at every pixel,
+// then the red half-sweep at the red pixels (a red update reads only its own b and the black
+// neighbours, which this kernel does not write).
+template <typename T, typename TF>
+__global__ void k_pdr_b_red(IterArgs A, bool has_w) {
+    const PView V = view_of(A);
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int H = V.g.H, W = V.g.W, P = V.g.pitch;
+    if (i >= H || j >= W) return;
+    if (V.done && *V.done) return;
+    float *tmp = V.tmp;
+    const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
+    const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
+    const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
+    for (int c = has_w ? 0 : 1; c < 3; ++c) {
+        tmp[c * plane + o] = pdr_rhs(ldT<TF>(V.f.f[XB[c]], o), div_at<T>(V.f.f[Y1[c]], V.f.f[Y2[c]], i, j, H, W, P), A.k.sigma);
+        tmp[(3 + c) * plane + o] = ldT<TF>(V.f.f[X[c]], o);
+    }
+    if (((i + j) & 1) == 0) {
+        const float st = A.k.sigma * A.k.tau;
+        for (int c = has_w ? 0 : 1; c < 3; ++c) stT<TF>(V.f.f[X[c]], o, gs_value<TF>(V, tmp, plane, c, i, j, st));
+    }
+}
+
+// Fused engine, last kernel of an iteration: the final red half-sweep and the Xbar / ybar updates.
+// X^{k+1} at a red pixel is its red update (black neighbours final); a black pixel's east and south
+// neighbours are red, so its thread recomputes their updates (the same value their own threads
+// store) instead of waiting for them.  This kernel writes only red pixels' X and reads only black
+// pixels' X, so no thread reads a value another thread of it writes.
+template <typename T, typename TF>
+__global__ void k_pdr_red_finish(IterArgs A, bool has_w) {
+    __shared__ double red[32];
+    const PView V = view_of(A);
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int H = V.g.H, W = V.g.W, P = V.g.pitch;
+    if (V.done && *V.done) return;
+    const float *tmp = V.tmp;
+    double res = 0.0;
+    if (i < H && j < W) {
+        const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
+        const float beta = A.k.beta, lam = A.k.lambda, sg = A.k.sigma, ta = A.k.tau, st = sg * ta;
+        const int X[3] = {F_W, F_U, F_V};
+        auto xnew = [&](int a, int b, int c) {
+            return ((a + b) & 1) == 0 ? gs_value<TF>(V, tmp, plane, c, a, b, st)
+                                      : ldT<TF>(V.f.f[X[c]], (size_t)a * P + b);
+        };
+        const bool hx = j < W - 1, hy = i < H - 1, is_red = ((i + j) & 1) == 0;
+        float x[3] = {0.f, 0.f, 0.f}, g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c = has_w ? 0 : 1; c < 3; ++c) {
+            x[c] = xnew(i, j, c);
+            g[2 * c] = hx ? xnew(i, j + 1, c) - x[c] : 0.f;
+            g[2 * c + 1] = hy ? xnew(i + 1, j, c) - x[c] : 0.f;
+        }
+        const float ix = ldT<T>(V.Ix, o), iy = ldT<T>(V.Iy, o), it = ldT<T>(V.It, o);
+        float xb[3] = {has_w ? ldT<TF>(V.f.f[F_WB], o) : 0.f, ldT<TF>(V.f.f[F_UB], o), ldT<TF>(V.f.f[F_VB], o)};
+        if (has_w) pdr_xbar<true>(x, xb, ix, iy, it, beta, lam, sg);
+        else pdr_xbar<false>(x, xb, ix, iy, it, beta, lam, sg);
+        const float y[6] = {has_w ? ldT<T>(V.f.f[F_P1], o) : 0.f, has_w ? ldT<T>(V.f.f[F_P2], o) : 0.f,
+                            ldT<T>(V.f.f[F_Q11], o), ldT<T>(V.f.f[F_Q12], o), ldT<T>(V.f.f[F_Q21], o),
+                            ldT<T>(V.f.f[F_Q22], o)};
+        float yn[6];
+        if (has_w) pdr_ybar<true>(y, g, ta, yn);
+        else pdr_ybar<false>(y, g, ta, yn);
+        if (is_red)
+            for (int c = has_w ? 0 : 1; c < 3; ++c) stT<TF>(V.f.f[X[c]], o, x[c]);
+        if (has_w) {
+            stT<TF>(V.f.f[F_WB], o, xb[0]);
+            stT<T>(V.f.f[F_P1], o, yn[0]);
+            stT<T>(V.f.f[F_P2], o, yn[1]);
+        }
+        stT<TF>(V.f.f[F_UB], o, xb[1]);
+        stT<TF>(V.f.f[F_VB], o, xb[2]);
+        stT<T>(V.f.f[F_Q11], o, yn[2]);
+        stT<T>(V.f.f[F_Q12], o, yn[3]);
+        stT<T>(V.f.f[F_Q21], o, yn[4]);
+        stT<T>(V.f.f[F_Q22], o, yn[5]);
+        const float dw = has_w ? x[0] - tmp[3 * plane + o] : 0.f;
+        const float du = x[1] - tmp[4 * plane + o], dv = x[2] - tmp[5 * plane + o];
+        res = (double)dw * dw + (double)du * du + (double)dv * dv;
+    }
+    if (A.partials) {
+        const double tot = block_sum(res, red);
+        if (threadIdx.x == 0 && threadIdx.y == 0) A.partials[partial_slot(V)] = tot;
+    }
+}
+
 // One red (colour 0) or black (colour 1) Gauss-Seidel half-sweep on (1 + st n_ij) x_ij - st sum x_nb = b_ij.
 template <typename T, typename TF>
 __global__ void k_gs_half(IterArgs A, int colour, bool has_w) {
@@ -167,22 +274,27 @@ __global__ void k_pdr_finish(IterArgs A, bool has_w) {
 template <typename T, typename TF> void launch_pdr_t(const IterArgs &a, bool literal, cudaStream_t s) {
     const bool has_w = a.k.beta != 0.f;
     dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + PY - 1) / PY, a.pairs ? a.ntiles : 1), blk(PX, PY);
-    k_pdr_b<T, TF><<<grid, blk, 0, s>>>(a, has_w);
     if (literal) {
+        k_pdr_b<T, TF><<<grid, blk, 0, s>>>(a, has_w);
         for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
             k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
             k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
             k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
             k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
         }
-    } else if (a.k.gs_sweeps > 0) {
-        k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
-        for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
-            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
-            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
-        }
+        k_pdr_finish<T, TF><<<grid, blk, 0, s>>>(a, has_w);
+        return;
     }
-    k_pdr_finish<T, TF><<<grid, blk, 0, s>>>(a, has_w);
+    // fused: R (B R)^n in 2n + 1 launches, the first R with the right-hand side, the last with
+    // the Xbar / ybar updates
+    IterArgs b = a;
+    b.partials = nullptr;
+    k_pdr_b_red<T, TF><<<grid, blk, 0, s>>>(b, has_w);
+    for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
+        k_gs_half<T, TF><<<grid, blk, 0, s>>>(b, 1, has_w);
+        if (sw + 1 < a.k.gs_sweeps) k_gs_half<T, TF><<<grid, blk, 0, s>>>(b, 0, has_w);
+    }
+    k_pdr_red_finish<T, TF><<<grid, blk, 0, s>>>(a, has_w);
 }
 
 }  // namespace
