@@ -76,6 +76,8 @@ __device__ __forceinline__ void y_update_q(float q11, float q12, float q21, floa
 // so the s-block proximal matrix c(diag(a~) - M_s) stays positive semidefinite;
 // then Lambda = (w, u, v) -= r c (A s^{k+1} - div y^{k+1}) (VARIANT 0) or
 // Lambda -= c (A s^{k+1} - rho div y^{k+1} - (1 - rho) A s^k) (VARIANT 1), A s = (beta, Ix, Iy) s.
+// VARIANT bit 0: rpADMMII; bit 1: the per-pixel a~ (a compile-time choice, so the one-launch-per-
+// iteration kernel carries no branch for it).
 // Updates w, u, v in place, returns s^{k+1} in s_new and the squared constraint residual
 // |A s^{k+1} - div y^{k+1}|^2.
 template <bool HAS_W, int VARIANT>
@@ -88,19 +90,19 @@ __device__ __forceinline__ float finish_pixel(float ix, float iy, float it, floa
     const float divt0 = fmaf(iy, dq2n, ix * dq1n);
     const float divt = HAS_W ? fmaf(beta, dpn, divt0) : divt0;
     float inv_at = K.inv_at, inv_atc = K.inv_atc;
-    if (K.per_pixel) {  // uniform over the launch
+    if (VARIANT & 2) {
         const float at = fmaxf(ms, 1e-12f);
         inv_at = __frcp_rn(at);
         inv_atc = __frcp_rn(at * K.cc);
     }
     float s;
-    if (VARIANT == 0) s = fmaf(fmaf(K.cc, divt, lin), inv_atc, fmaf(-ms, inv_at, 1.f) * s_old);
+    if ((VARIANT & 1) == 0) s = fmaf(fmaf(K.cc, divt, lin), inv_atc, fmaf(-ms, inv_at, 1.f) * s_old);
     else s = fmaf(fmaf(K.cc * K.rho, divt, lin), inv_atc, fmaf(-K.rho * ms, inv_at, 1.f) * s_old);
     s = fminf(fmaxf(s, -K.lam), K.lam);  // P_s: projection onto |s| <= lambda
     s_new = s;
     const float cw = HAS_W ? fmaf(beta, s, -dpn) : 0.f;
     const float cu = fmaf(ix, s, -dq1n), cv = fmaf(iy, s, -dq2n);
-    if (VARIANT == 0) {
+    if ((VARIANT & 1) == 0) {
         if (HAS_W) w = fmaf(-K.rc, cw, w);
         u = fmaf(-K.rc, cu, u);
         v = fmaf(-K.rc, cv, v);

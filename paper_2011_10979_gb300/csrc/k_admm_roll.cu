@@ -10,12 +10,12 @@ int admm_fused_strip_w() { return roll::SW; }
 int admm_fused_warps() { return roll::WARPS; }
 
 namespace {
-// TVL1_ADMM_ROWS_PER_WARP=1|2|4|8|16|32 pins the strip height (read once; for tuning sweeps).
+// TVL1_ADMM_ROWS_PER_WARP=1|2|8|32 pins the strip height (read once; for tuning sweeps).
 int forced_rows_per_warp() {
     static const int v = [] {
         const char *e = getenv("TVL1_ADMM_ROWS_PER_WARP");
         const int t = e ? atoi(e) : 0;
-        return (t == 1 || t == 2 || t == 4 || t == 8 || t == 16 || t == 32) ? t : 0;
+        return (t == 1 || t == 2 || t == 8 || t == 32) ? t : 0;
     }();
     return v;
 }

@@ -32,7 +32,7 @@
 
 namespace tvl1 {
 
-// Per storage type: launches k_admm_roll with TY rows per warp (TY in 1, 2, 4, 8, 16, 32).
+// Per storage type: launches k_admm_roll with TY rows per warp (TY in 1, 2, 8, 32).
 void roll_launch_f32(const IterArgs &a, int ty, cudaStream_t s);
 void roll_launch_f16(const IterArgs &a, int ty, bool flow32, cudaStream_t s);
 void roll_launch_bf16(const IterArgs &a, int ty, bool flow32, cudaStream_t s);
@@ -252,9 +252,7 @@ template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_ty(const
     switch (ty) {
     case 1: launch_t<T, TF, HAS_W, VARIANT, 1>(a, s); break;
     case 2: launch_t<T, TF, HAS_W, VARIANT, 2>(a, s); break;
-    case 4: launch_t<T, TF, HAS_W, VARIANT, 4>(a, s); break;
     case 8: launch_t<T, TF, HAS_W, VARIANT, 8>(a, s); break;
-    case 16: launch_t<T, TF, HAS_W, VARIANT, 16>(a, s); break;
     default: launch_t<T, TF, HAS_W, VARIANT, 32>(a, s); break;
     }
 }
@@ -262,11 +260,21 @@ template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_ty(const
 template <typename T, typename TF> void launch_m(const IterArgs &a, int ty, cudaStream_t s) {
     const bool has_w = a.k.beta != 0.f;
     if (a.k.method == 1) {
-        if (has_w) launch_ty<T, TF, true, 1>(a, ty, s);
-        else launch_ty<T, TF, false, 1>(a, ty, s);
+        if (a.k.a_tilde_mode == 1) {
+            if (has_w) launch_ty<T, TF, true, 3>(a, ty, s);
+            else launch_ty<T, TF, false, 3>(a, ty, s);
+        } else {
+            if (has_w) launch_ty<T, TF, true, 1>(a, ty, s);
+            else launch_ty<T, TF, false, 1>(a, ty, s);
+        }
     } else {
-        if (has_w) launch_ty<T, TF, true, 0>(a, ty, s);
-        else launch_ty<T, TF, false, 0>(a, ty, s);
+        if (a.k.a_tilde_mode == 1) {
+            if (has_w) launch_ty<T, TF, true, 2>(a, ty, s);
+            else launch_ty<T, TF, false, 2>(a, ty, s);
+        } else {
+            if (has_w) launch_ty<T, TF, true, 0>(a, ty, s);
+            else launch_ty<T, TF, false, 0>(a, ty, s);
+        }
     }
 }
 

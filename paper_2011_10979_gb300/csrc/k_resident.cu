@@ -316,8 +316,11 @@ __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
             float dpn, dq1n, dq2n;
             div_at(x, li, j, dpn, dq1n, dq2n);
             float w = S[S_W * PL + x], u = S[S_U * PL + x], v = S[S_V * PL + x], s_new;
-            res += finish_pixel<HAS_W, VARIANT>(S[S_IX * PL + x], S[S_IY * PL + x], S[S_IT * PL + x], S[S_S * PL + x],
-                                                w, u, v, dpn, dq1n, dq2n, K, s_new);
+            res += K.per_pixel  // uniform over the launch
+                       ? finish_pixel<HAS_W, VARIANT | 2>(S[S_IX * PL + x], S[S_IY * PL + x], S[S_IT * PL + x],
+                                                          S[S_S * PL + x], w, u, v, dpn, dq1n, dq2n, K, s_new)
+                       : finish_pixel<HAS_W, VARIANT>(S[S_IX * PL + x], S[S_IY * PL + x], S[S_IT * PL + x],
+                                                      S[S_S * PL + x], w, u, v, dpn, dq1n, dq2n, K, s_new);
             s_new = storage_round<T>(s_new);
             w = storage_round<TF>(w);
             u = storage_round<TF>(u);

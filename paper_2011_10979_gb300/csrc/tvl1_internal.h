@@ -86,7 +86,7 @@ struct IterArgs {
 };
 
 // Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w() output
-// columns and TY rows (TY = 1, 2 or 8 by default, chosen per level by admm_fused_tile_h); a block stacks
+// columns and TY rows (TY = 1, 2, 8 or 32, chosen per level by admm_fused_tile_h); a block stacks
 // admm_fused_warps() strips vertically.  A work-list entry (pair, tx, ty) is the block covering
 // columns [tx * strip_w, ...) and rows [ty * warps * TY, ...).
 int admm_fused_tile_h(Geom g);
