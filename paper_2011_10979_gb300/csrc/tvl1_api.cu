@@ -177,6 +177,8 @@ struct of_ctx {
     cudaStream_t cap = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::map<std::string, GraphEntry> graphs;
+    // the batch layout whose launch tables the arena holds (graphs of other layouts re-upload)
+    std::string tables_key;
     // serving loop state (tvl1_serve.cu)
     void *server = nullptr;
 };
@@ -189,6 +191,7 @@ void drop_graphs(of_ctx *ctx) {
         if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     }
     ctx->graphs.clear();
+    ctx->tables_key.clear();
 }
 
 of_status ensure_arena(of_ctx *ctx, size_t bytes) {
@@ -404,7 +407,10 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
             ps[k].resident = B.res[l][k];
         }
     }
+    // work already queued on any stream may still read another layout's tables in this region
+    OF_CUDA(cudaDeviceSynchronize());
     OF_CUDA(cudaMemcpy(ctx->arena + B.table_off, img.data(), img.size(), cudaMemcpyHostToDevice));
+    ctx->tables_key = B.key;
     return OF_OK;
 }
 
@@ -673,8 +679,16 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
 }
 
 of_status get_graph(of_ctx *ctx, const Batch &B, const of_params *p, cudaGraphExec_t *out, cudaGraph_t *graph_out = nullptr) {
+    // a single-pair solve lays its data out from the arena's start, over any batch's tables
+    if (B.n <= 1) ctx->tables_key.clear();
     auto it = ctx->graphs.find(B.key);
     if (it != ctx->graphs.end()) {
+        // a cached batch graph reads its tables from the arena: restore them if another batch
+        // layout has replaced them since
+        if (B.n > 1 && ctx->tables_key != B.key) {
+            of_status st = upload_tables(ctx, B, p);
+            if (st != OF_OK) return st;
+        }
         *out = it->second.exec;
         if (graph_out) *graph_out = it->second.graph;
         return OF_OK;

@@ -336,6 +336,22 @@ def test_batch_equals_single(ctx, name, prec, tol, engine):
         assert st["energy"] == pytest.approx(sst["energy"], rel=1e-12, abs=1e-12)
 
 
+def test_alternating_batch_layouts(ctx):
+    """Two batches of different layouts (and a single-pair solve) alternating in one context: each
+    replay of a cached batch graph finds its own launch tables again, although the other layout's
+    tables and the single solve's data overwrote them in between."""
+    pa = [synth.sinusoid_pair(seed=s) for s in range(3)]
+    pb = [synth.random_affine_rect_pair(96, 128, 2), synth.random_affine_rect_pair(250, 300, 3)]
+    P = flow.default_params(lam=2.0, iters=20, levels=3, warps=2)
+    ra = flow.of_solve_batch(ctx, [cu(p.I0) for p in pa], [cu(p.I1) for p in pa], P, stats=False)[0]
+    rb = flow.of_solve_batch(ctx, [cu(p.I0) for p in pb], [cu(p.I1) for p in pb], P, stats=False)[0]
+    flow.of_solve(ctx, cu(pb[1].I0), cu(pb[1].I1), P, stats=False)  # a single solve over the arena
+    ra2 = flow.of_solve_batch(ctx, [cu(p.I0) for p in pa], [cu(p.I1) for p in pa], P, stats=False)[0]
+    rb2 = flow.of_solve_batch(ctx, [cu(p.I0) for p in pb], [cu(p.I1) for p in pb], P, stats=False)[0]
+    assert all(torch.equal(x, y) for x, y in zip(ra, ra2))
+    assert all(torch.equal(x, y) for x, y in zip(rb, rb2))
+
+
 def test_invalid_arguments(ctx):
     pr = synth.sinusoid_pair()
     for bad in (dict(levels=0), dict(lam=-1.0), dict(eta=1.5), dict(method=7), dict(r=2.0),
