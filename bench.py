@@ -214,7 +214,7 @@ def run_ours(args):
     launches = flow.of_solve_kernel_count(ctx, H, W, P)
     full = args.legs == "all"
     roof = kernel_roofline(flow, torch, dev, pr) if full else None
-    t_plain = serving = serving50 = batch = batch_all16 = prec_line = solvers = None
+    t_plain = serving = serving50 = batch = batch_all16 = batch_fp32 = prec_line = solvers = None
     if full:
         # plain single-pair FP32 GPU path (one kernel per operator), same workload
         Pp = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
@@ -232,6 +232,7 @@ def run_ours(args):
         serving50 = serving_measure(flow, torch, dev, rate_hz=50.0)
         batch = batch_measure(flow, torch, dev, fp32_flow=1)
         batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
+        batch_fp32 = batch_measure(flow, torch, dev, prec=flow.OF_PREC_FP32)
         prec_line = precision_measure(flow, torch, dev)
         solvers = solvers_measure(flow, torch, dev, I0, I1, pr)
     if rank != 0:
@@ -263,6 +264,7 @@ def run_ours(args):
             "serving": serving,
             "serving_50hz": serving50,
             "batch_all16": batch_all16,
+            "batch_fp32": batch_fp32,
             "precision_1024x436": prec_line,
             "solvers_640x480": solvers,
             "cpu_baseline": cpu,

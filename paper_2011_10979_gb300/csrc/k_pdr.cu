@@ -75,8 +75,8 @@ __device__ __forceinline__ size_t partial_slot(const PView &V) {
 }
 
 // b_c = Xbar_c + sigma div ybar_c, and a copy of X^k for the residual (FP32 planes in tmp).
-template <typename T, typename TF>
-__global__ void k_pdr_b(IterArgs A, bool has_w) {
+template <typename T, typename TF, bool HAS_W>
+__global__ void k_pdr_b(IterArgs A) {
     const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
@@ -86,7 +86,8 @@ __global__ void k_pdr_b(IterArgs A, bool has_w) {
     const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
     const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
     const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
-    for (int c = has_w ? 0 : 1; c < 3; ++c) {
+#pragma unroll
+    for (int c = HAS_W ? 0 : 1; c < 3; ++c) {
         tmp[c * plane + o] = pdr_rhs(ldT<TF>(V.f.f[XB[c]], o), div_at<T>(V.f.f[Y1[c]], V.f.f[Y2[c]], i, j, H, W, P), A.k.sigma);
         tmp[(3 + c) * plane + o] = ldT<TF>(V.f.f[X[c]], o);
     }
@@ -114,8 +115,8 @@ __device__ __forceinline__ float gs_value(const PView &V, const float *tmp, size
 // Fused engine, first kernel of an iteration: b = Xbar + sigma div ybar and X^k at every pixel,
 // then the red half-sweep at the red pixels (a red update reads only its own b and the black
 // neighbours, which this kernel does not write).
-template <typename T, typename TF>
-__global__ void k_pdr_b_red(IterArgs A, bool has_w) {
+template <typename T, typename TF, bool HAS_W>
+__global__ void k_pdr_b_red(IterArgs A) {
     const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
@@ -125,13 +126,15 @@ __global__ void k_pdr_b_red(IterArgs A, bool has_w) {
     const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
     const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
     const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
-    for (int c = has_w ? 0 : 1; c < 3; ++c) {
+#pragma unroll
+    for (int c = HAS_W ? 0 : 1; c < 3; ++c) {
         tmp[c * plane + o] = pdr_rhs(ldT<TF>(V.f.f[XB[c]], o), div_at<T>(V.f.f[Y1[c]], V.f.f[Y2[c]], i, j, H, W, P), A.k.sigma);
         tmp[(3 + c) * plane + o] = ldT<TF>(V.f.f[X[c]], o);
     }
     if (((i + j) & 1) == 0) {
         const float st = A.k.sigma * A.k.tau;
-        for (int c = has_w ? 0 : 1; c < 3; ++c) stT<TF>(V.f.f[X[c]], o, gs_value<TF>(V, tmp, plane, c, i, j, st));
+#pragma unroll
+        for (int c = HAS_W ? 0 : 1; c < 3; ++c) stT<TF>(V.f.f[X[c]], o, gs_value<TF>(V, tmp, plane, c, i, j, st));
     }
 }
 
@@ -140,8 +143,8 @@ __global__ void k_pdr_b_red(IterArgs A, bool has_w) {
 // neighbours are red, so its thread recomputes their updates (the same value their own threads
 // store) instead of waiting for them.  This kernel writes only red pixels' X and reads only black
 // pixels' X, so no thread reads a value another thread of it writes.
-template <typename T, typename TF>
-__global__ void k_pdr_red_finish(IterArgs A, bool has_w) {
+template <typename T, typename TF, bool HAS_W>
+__global__ void k_pdr_red_finish(IterArgs A) {
     __shared__ double red[32];
     const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
@@ -159,24 +162,27 @@ __global__ void k_pdr_red_finish(IterArgs A, bool has_w) {
         };
         const bool hx = j < W - 1, hy = i < H - 1, is_red = ((i + j) & 1) == 0;
         float x[3] = {0.f, 0.f, 0.f}, g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int c = has_w ? 0 : 1; c < 3; ++c) {
+#pragma unroll
+        for (int c = HAS_W ? 0 : 1; c < 3; ++c) {
             x[c] = xnew(i, j, c);
             g[2 * c] = hx ? xnew(i, j + 1, c) - x[c] : 0.f;
             g[2 * c + 1] = hy ? xnew(i + 1, j, c) - x[c] : 0.f;
         }
         const float ix = ldT<T>(V.Ix, o), iy = ldT<T>(V.Iy, o), it = ldT<T>(V.It, o);
-        float xb[3] = {has_w ? ldT<TF>(V.f.f[F_WB], o) : 0.f, ldT<TF>(V.f.f[F_UB], o), ldT<TF>(V.f.f[F_VB], o)};
-        if (has_w) pdr_xbar<true>(x, xb, ix, iy, it, beta, lam, sg);
+        float xb[3] = {HAS_W ? ldT<TF>(V.f.f[F_WB], o) : 0.f, ldT<TF>(V.f.f[F_UB], o), ldT<TF>(V.f.f[F_VB], o)};
+        if (HAS_W) pdr_xbar<true>(x, xb, ix, iy, it, beta, lam, sg);
         else pdr_xbar<false>(x, xb, ix, iy, it, beta, lam, sg);
-        const float y[6] = {has_w ? ldT<T>(V.f.f[F_P1], o) : 0.f, has_w ? ldT<T>(V.f.f[F_P2], o) : 0.f,
+        const float y[6] = {HAS_W ? ldT<T>(V.f.f[F_P1], o) : 0.f, HAS_W ? ldT<T>(V.f.f[F_P2], o) : 0.f,
                             ldT<T>(V.f.f[F_Q11], o), ldT<T>(V.f.f[F_Q12], o), ldT<T>(V.f.f[F_Q21], o),
                             ldT<T>(V.f.f[F_Q22], o)};
         float yn[6];
-        if (has_w) pdr_ybar<true>(y, g, ta, yn);
+        if (HAS_W) pdr_ybar<true>(y, g, ta, yn);
         else pdr_ybar<false>(y, g, ta, yn);
-        if (is_red)
-            for (int c = has_w ? 0 : 1; c < 3; ++c) stT<TF>(V.f.f[X[c]], o, x[c]);
-        if (has_w) {
+        if (is_red) {
+#pragma unroll
+            for (int c = HAS_W ? 0 : 1; c < 3; ++c) stT<TF>(V.f.f[X[c]], o, x[c]);
+        }
+        if (HAS_W) {
             stT<TF>(V.f.f[F_WB], o, xb[0]);
             stT<T>(V.f.f[F_P1], o, yn[0]);
             stT<T>(V.f.f[F_P2], o, yn[1]);
@@ -187,7 +193,7 @@ __global__ void k_pdr_red_finish(IterArgs A, bool has_w) {
         stT<T>(V.f.f[F_Q12], o, yn[3]);
         stT<T>(V.f.f[F_Q21], o, yn[4]);
         stT<T>(V.f.f[F_Q22], o, yn[5]);
-        const float dw = has_w ? x[0] - tmp[3 * plane + o] : 0.f;
+        const float dw = HAS_W ? x[0] - tmp[3 * plane + o] : 0.f;
         const float du = x[1] - tmp[4 * plane + o], dv = x[2] - tmp[5 * plane + o];
         res = (double)dw * dw + (double)du * du + (double)dv * dv;
     }
@@ -198,8 +204,8 @@ __global__ void k_pdr_red_finish(IterArgs A, bool has_w) {
 }
 
 // One red (colour 0) or black (colour 1) Gauss-Seidel half-sweep on (1 + st n_ij) x_ij - st sum x_nb = b_ij.
-template <typename T, typename TF>
-__global__ void k_gs_half(IterArgs A, int colour, bool has_w) {
+template <typename T, typename TF, bool HAS_W>
+__global__ void k_gs_half(IterArgs A, int colour) {
     const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
@@ -209,7 +215,8 @@ __global__ void k_gs_half(IterArgs A, int colour, bool has_w) {
     const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
     const float st = A.k.sigma * A.k.tau;
     const int X[3] = {F_W, F_U, F_V};
-    for (int c = has_w ? 0 : 1; c < 3; ++c) {
+#pragma unroll
+    for (int c = HAS_W ? 0 : 1; c < 3; ++c) {
         const void *x = V.f.f[X[c]];
         float acc = 0.f;
         int nb = 0;
@@ -222,8 +229,8 @@ __global__ void k_gs_half(IterArgs A, int colour, bool has_w) {
 }
 
 // Xbar update through the L1 resolvent, ybar update, residual partial ||X^{k+1} - X^k||^2.
-template <typename T, typename TF>
-__global__ void k_pdr_finish(IterArgs A, bool has_w) {
+template <typename T, typename TF, bool HAS_W>
+__global__ void k_pdr_finish(IterArgs A) {
     __shared__ double red[32];
     const PView V = view_of(A);
     const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
@@ -235,25 +242,25 @@ __global__ void k_pdr_finish(IterArgs A, bool has_w) {
         const size_t o = (size_t)i * P + j, plane = (size_t)H * P;
         const float beta = A.k.beta, lam = A.k.lambda, sg = A.k.sigma, ta = A.k.tau;
         const float ix = ldT<T>(V.Ix, o), iy = ldT<T>(V.Iy, o), it = ldT<T>(V.It, o);
-        const float x[3] = {has_w ? ldT<TF>(V.f.f[F_W], o) : 0.f, ldT<TF>(V.f.f[F_U], o), ldT<TF>(V.f.f[F_V], o)};
-        float xb[3] = {has_w ? ldT<TF>(V.f.f[F_WB], o) : 0.f, ldT<TF>(V.f.f[F_UB], o), ldT<TF>(V.f.f[F_VB], o)};
-        if (has_w) pdr_xbar<true>(x, xb, ix, iy, it, beta, lam, sg);
+        const float x[3] = {HAS_W ? ldT<TF>(V.f.f[F_W], o) : 0.f, ldT<TF>(V.f.f[F_U], o), ldT<TF>(V.f.f[F_V], o)};
+        float xb[3] = {HAS_W ? ldT<TF>(V.f.f[F_WB], o) : 0.f, ldT<TF>(V.f.f[F_UB], o), ldT<TF>(V.f.f[F_VB], o)};
+        if (HAS_W) pdr_xbar<true>(x, xb, ix, iy, it, beta, lam, sg);
         else pdr_xbar<false>(x, xb, ix, iy, it, beta, lam, sg);
-        if (has_w) stT<TF>(V.f.f[F_WB], o, xb[0]);
+        if (HAS_W) stT<TF>(V.f.f[F_WB], o, xb[0]);
         stT<TF>(V.f.f[F_UB], o, xb[1]);
         stT<TF>(V.f.f[F_VB], o, xb[2]);
         const bool hx = j < W - 1, hy = i < H - 1;
         auto gx = [&](int f, float x0) { return hx ? ldT<TF>(V.f.f[f], o + 1) - x0 : 0.f; };
         auto gy = [&](int f, float x0) { return hy ? ldT<TF>(V.f.f[f], o + P) - x0 : 0.f; };
-        const float g[6] = {has_w ? gx(F_W, x[0]) : 0.f, has_w ? gy(F_W, x[0]) : 0.f, gx(F_U, x[1]), gy(F_U, x[1]),
+        const float g[6] = {HAS_W ? gx(F_W, x[0]) : 0.f, HAS_W ? gy(F_W, x[0]) : 0.f, gx(F_U, x[1]), gy(F_U, x[1]),
                             gx(F_V, x[2]), gy(F_V, x[2])};
-        const float y[6] = {has_w ? ldT<T>(V.f.f[F_P1], o) : 0.f, has_w ? ldT<T>(V.f.f[F_P2], o) : 0.f,
+        const float y[6] = {HAS_W ? ldT<T>(V.f.f[F_P1], o) : 0.f, HAS_W ? ldT<T>(V.f.f[F_P2], o) : 0.f,
                             ldT<T>(V.f.f[F_Q11], o), ldT<T>(V.f.f[F_Q12], o), ldT<T>(V.f.f[F_Q21], o),
                             ldT<T>(V.f.f[F_Q22], o)};
         float yn[6];
-        if (has_w) pdr_ybar<true>(y, g, ta, yn);
+        if (HAS_W) pdr_ybar<true>(y, g, ta, yn);
         else pdr_ybar<false>(y, g, ta, yn);
-        if (has_w) {
+        if (HAS_W) {
             stT<T>(V.f.f[F_P1], o, yn[0]);
             stT<T>(V.f.f[F_P2], o, yn[1]);
         }
@@ -261,7 +268,7 @@ __global__ void k_pdr_finish(IterArgs A, bool has_w) {
         stT<T>(V.f.f[F_Q12], o, yn[3]);
         stT<T>(V.f.f[F_Q21], o, yn[4]);
         stT<T>(V.f.f[F_Q22], o, yn[5]);
-        const float dw = has_w ? x[0] - tmp[3 * plane + o] : 0.f;
+        const float dw = HAS_W ? x[0] - tmp[3 * plane + o] : 0.f;
         const float du = x[1] - tmp[4 * plane + o], dv = x[2] - tmp[5 * plane + o];
         res = (double)dw * dw + (double)du * du + (double)dv * dv;
     }
@@ -271,30 +278,34 @@ __global__ void k_pdr_finish(IterArgs A, bool has_w) {
     }
 }
 
-template <typename T, typename TF> void launch_pdr_t(const IterArgs &a, bool literal, cudaStream_t s) {
-    const bool has_w = a.k.beta != 0.f;
+template <typename T, typename TF, bool HAS_W> void launch_pdr_w(const IterArgs &a, bool literal, cudaStream_t s) {
     dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + PY - 1) / PY, a.pairs ? a.ntiles : 1), blk(PX, PY);
     if (literal) {
-        k_pdr_b<T, TF><<<grid, blk, 0, s>>>(a, has_w);
+        k_pdr_b<T, TF, HAS_W><<<grid, blk, 0, s>>>(a);
         for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
-            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
-            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
-            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 1, has_w);
-            k_gs_half<T, TF><<<grid, blk, 0, s>>>(a, 0, has_w);
+            k_gs_half<T, TF, HAS_W><<<grid, blk, 0, s>>>(a, 0);
+            k_gs_half<T, TF, HAS_W><<<grid, blk, 0, s>>>(a, 1);
+            k_gs_half<T, TF, HAS_W><<<grid, blk, 0, s>>>(a, 1);
+            k_gs_half<T, TF, HAS_W><<<grid, blk, 0, s>>>(a, 0);
         }
-        k_pdr_finish<T, TF><<<grid, blk, 0, s>>>(a, has_w);
+        k_pdr_finish<T, TF, HAS_W><<<grid, blk, 0, s>>>(a);
         return;
     }
     // fused: R (B R)^n in 2n + 1 launches, the first R with the right-hand side, the last with
     // the Xbar / ybar updates
     IterArgs b = a;
     b.partials = nullptr;
-    k_pdr_b_red<T, TF><<<grid, blk, 0, s>>>(b, has_w);
+    k_pdr_b_red<T, TF, HAS_W><<<grid, blk, 0, s>>>(b);
     for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
-        k_gs_half<T, TF><<<grid, blk, 0, s>>>(b, 1, has_w);
-        if (sw + 1 < a.k.gs_sweeps) k_gs_half<T, TF><<<grid, blk, 0, s>>>(b, 0, has_w);
+        k_gs_half<T, TF, HAS_W><<<grid, blk, 0, s>>>(b, 1);
+        if (sw + 1 < a.k.gs_sweeps) k_gs_half<T, TF, HAS_W><<<grid, blk, 0, s>>>(b, 0);
     }
-    k_pdr_red_finish<T, TF><<<grid, blk, 0, s>>>(a, has_w);
+    k_pdr_red_finish<T, TF, HAS_W><<<grid, blk, 0, s>>>(a);
+}
+
+template <typename T, typename TF> void launch_pdr_t(const IterArgs &a, bool literal, cudaStream_t s) {
+    if (a.k.beta != 0.f) launch_pdr_w<T, TF, true>(a, literal, s);
+    else launch_pdr_w<T, TF, false>(a, literal, s);
 }
 
 }  // namespace
