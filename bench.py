@@ -494,32 +494,11 @@ def kernel_roofline(flow, torch, dev, pr, reps=20):
     per = (t[220] - t[20]) / 200.0
     bytes_per_launch = 92.0 * H * W
     achieved = bytes_per_launch / per / 1e9
-    l2 = l2_copy_gbs(torch, dev, bytes_per_launch)
     return {"kernel": "k_admm_roll<float,float,1,0,8> (640x480 level)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
             "traffic": ROLL_640_DRAM_BYTES, "us_per_launch": per * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch,
             "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 200",
-            "l2_copy_gbs": l2, "frac_of_l2_copy": achieved / l2,
-            "note": "the 640x480 level's 28 MB state stays in the 129 MB L2, so the L2 copy rate is the tighter roof"}
-
-
-def l2_copy_gbs(torch, dev, nbytes, reps=200):
-    """Device-to-device copy rate of a buffer of the kernel's traffic size that stays in L2 (read +
-    write bytes per second, CUDA events, 200 back-to-back copies after warm-up)."""
-    n = int(nbytes // 2 // 4)
-    a = torch.empty(n, dtype=torch.float32, device=dev).fill_(1.0)
-    b = torch.empty_like(a)
-    for _ in range(10):
-        b.copy_(a)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        b.copy_(a)
-    e1.record()
-    torch.cuda.synchronize(dev)
-    t = e0.elapsed_time(e1) / reps / 1e3
-    return 2.0 * n * 4 / t / 1e9
+            "note": "the 640x480 level's 28 MB state stays in the 129 MB L2 between iterations"}
 
 
 def main():
