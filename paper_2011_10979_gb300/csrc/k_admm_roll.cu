@@ -6,18 +6,7 @@
 
 namespace tvl1 {
 
-// Columns per lane for a strip height: two (aligned pairs, 60 output columns per strip) for the
-// tall strips of large levels, one (29 output columns) otherwise.  TVL1_ADMM_TWO_COLUMNS=0 keeps
-// one column everywhere (read once; for tuning sweeps).
-int admm_fused_cols(int ty) {
-    static const bool two = [] {
-        const char *e = getenv("TVL1_ADMM_TWO_COLUMNS");
-        return !(e && e[0] == '0');
-    }();
-    return (two && ty >= 8) ? 2 : 1;
-}
-
-int admm_fused_strip_w(int ty) { return admm_fused_cols(ty) == 2 ? roll::SW2 : roll::SW; }
+int admm_fused_strip_w() { return roll::SW; }
 int admm_fused_warps() { return roll::WARPS; }
 
 namespace {
@@ -53,15 +42,15 @@ int admm_fused_rows_per_warp(long strip_rows) {
 int admm_fused_tile_h(Geom g) { return admm_fused_rows_per_warp((long)((g.W + roll::SW - 1) / roll::SW) * g.H); }
 
 int admm_fused_blocks(Geom g) {
-    const int th = admm_fused_tile_h(g), sw = admm_fused_strip_w(th);
-    return ((g.W + sw - 1) / sw) * ((g.H + th * roll::WARPS - 1) / (th * roll::WARPS));
+    const int th = admm_fused_tile_h(g);
+    return ((g.W + roll::SW - 1) / roll::SW) * ((g.H + th * roll::WARPS - 1) / (th * roll::WARPS));
 }
 
 void launch_admm_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
-    const int ty = a.tiles ? a.tile_h : admm_fused_tile_h(a.g), cols = admm_fused_cols(ty);
-    if (prec == PREC_F32) roll_launch_f32(a, ty, cols, s);
-    else if (prec == PREC_F16) roll_launch_f16(a, ty, cols, prec_flow == PREC_F32, s);
-    else roll_launch_bf16(a, ty, cols, prec_flow == PREC_F32, s);
+    const int ty = a.tiles ? a.tile_h : admm_fused_tile_h(a.g);
+    if (prec == PREC_F32) roll_launch_f32(a, ty, s);
+    else if (prec == PREC_F16) roll_launch_f16(a, ty, prec_flow == PREC_F32, s);
+    else roll_launch_bf16(a, ty, prec_flow == PREC_F32, s);
 }
 
 }  // namespace tvl1

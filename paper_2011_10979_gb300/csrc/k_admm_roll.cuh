@@ -32,17 +32,15 @@
 
 namespace tvl1 {
 
-// Per storage type: launches k_admm_roll with TY rows per warp (TY in 1, 2, 8, 32) and COLS
-// columns per lane (2 only with TY 8 or 32).
-void roll_launch_f32(const IterArgs &a, int ty, int cols, cudaStream_t s);
-void roll_launch_f16(const IterArgs &a, int ty, int cols, bool flow32, cudaStream_t s);
-void roll_launch_bf16(const IterArgs &a, int ty, int cols, bool flow32, cudaStream_t s);
+// Per storage type: launches k_admm_roll with TY rows per warp (TY in 1, 2, 8, 32).
+void roll_launch_f32(const IterArgs &a, int ty, cudaStream_t s);
+void roll_launch_f16(const IterArgs &a, int ty, bool flow32, cudaStream_t s);
+void roll_launch_bf16(const IterArgs &a, int ty, bool flow32, cudaStream_t s);
 
 namespace roll {
 
 constexpr int WARPS = 4;          // warps per block, stacked vertically (one strip each)
-constexpr int SW = 29;            // output columns per strip, one column per lane
-constexpr int SW2 = 60;           // output columns per strip, two columns per lane (even: aligned pairs)
+constexpr int SW = 29;            // output columns per strip
 constexpr unsigned FULL = 0xffffffffu;
 
 // The values of one row at this lane's column.
@@ -179,196 +177,7 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
     return res;
 }
 
-// ------------------------------------------------------------------ two columns per lane
-// The same iteration with lane l holding the adjacent columns c = c0 + 2l (A) and c + 1 (B): the
-// pair is loaded and stored as one aligned vector, A's east neighbour is B and B's west neighbour
-// is A in the same lane, so per pixel the loads, stores and shuffles halve.  A strip is 64 columns
-// (c0 even) with 60 output columns (lanes 1..30); lanes 0 and 31 supply the stencil halo.  The
-// per-pixel arithmetic is the same helper calls as in strip(), so the results are identical.
-struct Row2 {
-    float2 p1, p2, q11, q12, q21, q22, s, w, u, v, ix, iy, it;
-};
-
-template <typename T, typename TF, bool HAS_W, bool INT>
-__device__ __forceinline__ void load_row2(Row2 &R, const void *const *src, int i, int c, int H, int W, int P) {
-    // c is even and the row pitch is a multiple of 64 elements, so (c, c + 1) is an aligned pair
-    // inside the row whenever c is inside the image; B beyond the right border reads as zero
-    const bool ok = INT || (i >= 0 && i < H && c >= 0 && c < W);
-    const bool okB = INT || c + 1 < W;
-    const size_t o = ok ? (size_t)i * P + c : 0;
-    const float2 z = make_float2(0.f, 0.f);
-    auto L = [&](int k, bool tf) {
-        float2 v = ok ? (tf ? ldT2<TF>(src[k], o) : ldT2<T>(src[k], o)) : z;
-        if (!okB) v.y = 0.f;
-        return v;
-    };
-    R.p1 = HAS_W ? L(0, false) : z;
-    R.p2 = HAS_W ? L(1, false) : z;
-    R.q11 = L(2, false);
-    R.q12 = L(3, false);
-    R.q21 = L(4, false);
-    R.q22 = L(5, false);
-    R.s = L(6, false);
-    R.ix = L(7, false);
-    R.iy = L(8, false);
-    R.it = L(9, false);
-    R.w = HAS_W ? L(10, true) : z;
-    R.u = L(11, true);
-    R.v = L(12, true);
-}
-
-template <typename T, typename TF, bool HAS_W, int VARIANT, int TY, bool INT>
-__device__ __forceinline__ float strip2(const void *const *src, void *const *dst, int H, int W, int P, int c0, int y0,
-                                        int lane, const Coefs &K, float at) {
-    const int c = c0 + 2 * lane;               // column A; B is c + 1
-    const bool inA = INT || (c >= 0 && c < W), inB = INT || (c >= 0 && c + 1 < W);
-    const bool out_lane = lane >= 1 && lane <= 30;
-    const bool exA = INT || c + 1 < W, wxA = INT || c > 0;   // A's east (= B) / west neighbour inside
-    const bool exB = INT || c + 2 < W;                       // B's east neighbour inside (its west is A)
-    const StepK SK = step_coefs(K, at);
-
-    constexpr int NROWS = TY + 3;
-    constexpr int UNROLL = TY <= 8 ? NROWS : 4;
-    Row2 prev{}, cur{}, n1{}, n2{};
-    float2 dp_prev{0.f, 0.f}, dq1_prev{0.f, 0.f}, dq2_prev{0.f, 0.f};   // div y^k on row i-1
-    float2 six_prev{0.f, 0.f}, siy_prev{0.f, 0.f};                      // (s Ix, s Iy) on row i-1
-    float2 yp2_n{0.f, 0.f}, yq12_n{0.f, 0.f}, yq22_n{0.f, 0.f};         // y^{k+1} on the row above
-    float res = 0.f;
-
-    load_row2<T, TF, HAS_W, INT>(n1, src, y0 - 2, c, H, W, P);
-    load_row2<T, TF, HAS_W, INT>(n2, src, y0 - 1, c, H, W, P);
-#pragma unroll UNROLL
-    for (int k = 0; k < NROWS; ++k) {
-        const int i = y0 - 2 + k;
-        prev = cur;
-        cur = n1;
-        n1 = n2;
-        if (k + 2 < NROWS) load_row2<T, TF, HAS_W, INT>(n2, src, i + 2, c, H, W, P);
-        if (!INT && i >= H + 1) break;
-        // ---- div y^k on row i (A's west = B of the lane to the left; B's west = A)
-        const bool rin = INT || (i >= 0 && i < H), ey = INT || i < H - 1, ny = INT || i > 0;
-        const float p1w = __shfl_up_sync(FULL, cur.p1.y, 1), q11w = __shfl_up_sync(FULL, cur.q11.y, 1);
-        const float q21w = __shfl_up_sync(FULL, cur.q21.y, 1);
-        float2 dp{0.f, 0.f}, dq1{0.f, 0.f}, dq2{0.f, 0.f};
-        if (rin && inA) {
-            if (HAS_W) dp.x = div2(exA ? cur.p1.x : 0.f, wxA ? p1w : 0.f, ey ? cur.p2.x : 0.f, ny ? prev.p2.x : 0.f);
-            dq1.x = div2(exA ? cur.q11.x : 0.f, wxA ? q11w : 0.f, ey ? cur.q12.x : 0.f, ny ? prev.q12.x : 0.f);
-            dq2.x = div2(exA ? cur.q21.x : 0.f, wxA ? q21w : 0.f, ey ? cur.q22.x : 0.f, ny ? prev.q22.x : 0.f);
-        }
-        if (rin && inB) {
-            if (HAS_W) dp.y = div2(exB ? cur.p1.y : 0.f, cur.p1.x, ey ? cur.p2.y : 0.f, ny ? prev.p2.y : 0.f);
-            dq1.y = div2(exB ? cur.q11.y : 0.f, cur.q11.x, ey ? cur.q12.y : 0.f, ny ? prev.q12.y : 0.f);
-            dq2.y = div2(exB ? cur.q21.y : 0.f, cur.q21.x, ey ? cur.q22.y : 0.f, ny ? prev.q22.y : 0.f);
-        }
-        const float2 six_cur = make_float2(__fmul_rn(cur.s.x, cur.ix.x), __fmul_rn(cur.s.y, cur.ix.y));
-        const float2 siy_cur = make_float2(__fmul_rn(cur.s.x, cur.iy.x), __fmul_rn(cur.s.y, cur.iy.y));
-        // ---- y^{k+1} on row i-1 (A's east = B; B's east = A of the lane to the right)
-        const int im = i - 1;
-        const bool rim = INT || (im >= 0 && im < H);
-        const bool pinA = rim && inA, pinB = rim && inB;
-        const bool hy = INT || im < H - 1;
-        const float dpE = __shfl_down_sync(FULL, dp_prev.x, 1), dq1E = __shfl_down_sync(FULL, dq1_prev.x, 1);
-        const float dq2E = __shfl_down_sync(FULL, dq2_prev.x, 1);
-        const float sE = __shfl_down_sync(FULL, prev.s.x, 1), wE = __shfl_down_sync(FULL, prev.w.x, 1);
-        const float uE = __shfl_down_sync(FULL, prev.u.x, 1), vE = __shfl_down_sync(FULL, prev.v.x, 1);
-        const float sixE = __shfl_down_sync(FULL, six_prev.x, 1), siyE = __shfl_down_sync(FULL, siy_prev.x, 1);
-        float2 np1{0.f, 0.f}, np2{0.f, 0.f}, nq11{0.f, 0.f}, nq12{0.f, 0.f}, nq21{0.f, 0.f}, nq22{0.f, 0.f};
-        // one pixel's y-update given its own (x0 ...) and east (xe ...) values
-        auto yupd = [&](bool ex, float p1, float p2, float q11, float q12, float q21, float q22, float d0, float de,
-                        float dsouth, float d10, float d1e, float d1s, float d20, float d2e, float d2s, float s0,
-                        float se, float ss, float w0, float we, float ws, float u0, float ue, float us, float v0,
-                        float ve, float vs, float x0, float xe, float xs, float z0, float ze, float zs, float &o1,
-                        float &o2, float &o11, float &o12, float &o21, float &o22) {
-            if (HAS_W) {
-                const float gdx = ex ? de - d0 : 0.f, gdy = hy ? dsouth - d0 : 0.f;
-                const float wx_ = ex ? we - w0 : 0.f, wy_ = hy ? ws - w0 : 0.f;
-                const float sx_ = ex ? se - s0 : 0.f, sy_ = hy ? ss - s0 : 0.f;
-                y_update_p(p1, p2, gdx, gdy, wx_, wy_, sx_, sy_, SK, o1, o2);
-            }
-            const float sixx = ex ? xe - x0 : 0.f, sixy = hy ? xs - x0 : 0.f;
-            const float siyx = ex ? ze - z0 : 0.f, siyy = hy ? zs - z0 : 0.f;
-            const float g1x = ex ? d1e - d10 : 0.f, g1y = hy ? d1s - d10 : 0.f;
-            const float g2x = ex ? d2e - d20 : 0.f, g2y = hy ? d2s - d20 : 0.f;
-            const float ux = ex ? ue - u0 : 0.f, uy = hy ? us - u0 : 0.f;
-            const float vx = ex ? ve - v0 : 0.f, vy = hy ? vs - v0 : 0.f;
-            y_update_q(q11, q12, q21, q22, g1x, g1y, g2x, g2y, ux, uy, vx, vy, sixx, sixy, siyx, siyy, SK, o11, o12,
-                       o21, o22);
-        };
-        if (pinA)
-            yupd(exA, prev.p1.x, prev.p2.x, prev.q11.x, prev.q12.x, prev.q21.x, prev.q22.x, dp_prev.x, dp_prev.y, dp.x,
-                 dq1_prev.x, dq1_prev.y, dq1.x, dq2_prev.x, dq2_prev.y, dq2.x, prev.s.x, prev.s.y, cur.s.x, prev.w.x,
-                 prev.w.y, cur.w.x, prev.u.x, prev.u.y, cur.u.x, prev.v.x, prev.v.y, cur.v.x, six_prev.x, six_prev.y,
-                 six_cur.x, siy_prev.x, siy_prev.y, siy_cur.x, np1.x, np2.x, nq11.x, nq12.x, nq21.x, nq22.x);
-        if (pinB)
-            yupd(exB, prev.p1.y, prev.p2.y, prev.q11.y, prev.q12.y, prev.q21.y, prev.q22.y, dp_prev.y, dpE, dp.y,
-                 dq1_prev.y, dq1E, dq1.y, dq2_prev.y, dq2E, dq2.y, prev.s.y, sE, cur.s.y, prev.w.y, wE, cur.w.y,
-                 prev.u.y, uE, cur.u.y, prev.v.y, vE, cur.v.y, six_prev.y, sixE, six_cur.y, siy_prev.y, siyE,
-                 siy_cur.y, np1.y, np2.y, nq11.y, nq12.y, nq21.y, nq22.y);
-        // ---- finish row i-1 (A's west = B of the lane to the left)
-        const float np1W = __shfl_up_sync(FULL, np1.y, 1), nq11W = __shfl_up_sync(FULL, nq11.y, 1);
-        const float nq21W = __shfl_up_sync(FULL, nq21.y, 1);
-        const bool row_out = out_lane && im >= y0 && im < y0 + TY;
-        if (row_out && (pinA || pinB)) {
-            const bool nyy = INT || im > 0;
-            float2 w = prev.w, u = prev.u, v = prev.v, sn{0.f, 0.f};
-            if (pinA) {
-                float dpn = 0.f;
-                if (HAS_W) dpn = div2(exA ? np1.x : 0.f, wxA ? np1W : 0.f, hy ? np2.x : 0.f, nyy ? yp2_n.x : 0.f);
-                const float dq1n = div2(exA ? nq11.x : 0.f, wxA ? nq11W : 0.f, hy ? nq12.x : 0.f, nyy ? yq12_n.x : 0.f);
-                const float dq2n = div2(exA ? nq21.x : 0.f, wxA ? nq21W : 0.f, hy ? nq22.x : 0.f, nyy ? yq22_n.x : 0.f);
-                res += finish_pixel<HAS_W, VARIANT>(prev.ix.x, prev.iy.x, prev.it.x, prev.s.x, w.x, u.x, v.x, dpn, dq1n,
-                                                    dq2n, SK, sn.x);
-            }
-            if (pinB) {
-                float dpn = 0.f;
-                if (HAS_W) dpn = div2(exB ? np1.y : 0.f, np1.x, hy ? np2.y : 0.f, nyy ? yp2_n.y : 0.f);
-                const float dq1n = div2(exB ? nq11.y : 0.f, nq11.x, hy ? nq12.y : 0.f, nyy ? yq12_n.y : 0.f);
-                const float dq2n = div2(exB ? nq21.y : 0.f, nq21.x, hy ? nq22.y : 0.f, nyy ? yq22_n.y : 0.f);
-                res += finish_pixel<HAS_W, VARIANT>(prev.ix.y, prev.iy.y, prev.it.y, prev.s.y, w.y, u.y, v.y, dpn, dq1n,
-                                                    dq2n, SK, sn.y);
-            }
-            const size_t o = (size_t)im * P + c;
-            if (pinA && pinB) {
-                if (HAS_W) {
-                    stT2<T>(dst[F_P1], o, np1);
-                    stT2<T>(dst[F_P2], o, np2);
-                    stT2<TF>(dst[F_W], o, w);
-                }
-                stT2<T>(dst[F_Q11], o, nq11);
-                stT2<T>(dst[F_Q12], o, nq12);
-                stT2<T>(dst[F_Q21], o, nq21);
-                stT2<T>(dst[F_Q22], o, nq22);
-                stT2<T>(dst[F_S], o, sn);
-                stT2<TF>(dst[F_U], o, u);
-                stT2<TF>(dst[F_V], o, v);
-            } else {  // only A inside the image (B beyond the right border)
-                if (HAS_W) {
-                    stT<T>(dst[F_P1], o, np1.x);
-                    stT<T>(dst[F_P2], o, np2.x);
-                    stT<TF>(dst[F_W], o, w.x);
-                }
-                stT<T>(dst[F_Q11], o, nq11.x);
-                stT<T>(dst[F_Q12], o, nq12.x);
-                stT<T>(dst[F_Q21], o, nq21.x);
-                stT<T>(dst[F_Q22], o, nq22.x);
-                stT<T>(dst[F_S], o, sn.x);
-                stT<TF>(dst[F_U], o, u.x);
-                stT<TF>(dst[F_V], o, v.x);
-            }
-        }
-        yp2_n = np2;
-        yq12_n = nq12;
-        yq22_n = nq22;
-        dp_prev = dp;
-        dq1_prev = dq1;
-        dq2_prev = dq2;
-        six_prev = six_cur;
-        siy_prev = siy_cur;
-    }
-    return res;
-}
-
-template <typename T, typename TF, bool HAS_W, int VARIANT, int TY, int COLS>
+template <typename T, typename TF, bool HAS_W, int VARIANT, int TY>
 __global__ void __launch_bounds__(WARPS * 32) k_admm_roll(IterArgs A) {
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -421,64 +230,50 @@ __global__ void __launch_bounds__(WARPS * 32) k_admm_roll(IterArgs A) {
     const float at = a_tilde_of(A.k, msp);
     if (stopped) return;  // uniform per block: the pair's warp met its stopping test
 
-    const int c0 = sx * (COLS == 1 ? SW : SW2) - 2;  // first column of the strip
-    const int y0 = sy * TY;                          // first output row of the strip
-    // interior strip: columns c0 .. c0 + 32 COLS - 1 and rows y0-2 .. y0+TY all away from the border
-    const bool interior = c0 >= 1 && c0 + 32 * COLS <= W - 1 && y0 >= 2 && y0 + TY <= H - 2;
-    float res;
-    if (COLS == 1)
-        res = interior ? strip<T, TF, HAS_W, VARIANT, TY, true>(src, dst, H, W, P, c0, y0, lane, A.k, at)
-                       : strip<T, TF, HAS_W, VARIANT, TY, false>(src, dst, H, W, P, c0, y0, lane, A.k, at);
-    else
-        res = interior ? strip2<T, TF, HAS_W, VARIANT, TY, true>(src, dst, H, W, P, c0, y0, lane, A.k, at)
-                       : strip2<T, TF, HAS_W, VARIANT, TY, false>(src, dst, H, W, P, c0, y0, lane, A.k, at);
+    const int c0 = sx * SW - 2;                // first column of the strip
+    const int y0 = sy * TY;                    // first output row of the strip
+    // interior strip: columns c0 .. c0+31 and rows y0-2 .. y0+TY all away from the image border
+    const bool interior = c0 >= 1 && c0 + 32 <= W - 1 && y0 >= 2 && y0 + TY <= H - 2;
+    const float res = interior ? strip<T, TF, HAS_W, VARIANT, TY, true>(src, dst, H, W, P, c0, y0, lane, A.k, at)
+                               : strip<T, TF, HAS_W, VARIANT, TY, false>(src, dst, H, W, P, c0, y0, lane, A.k, at);
     if (A.partials) {
         const double tot = block_sum((double)res, red);
         if (threadIdx.x == 0) A.partials[blockIdx.x + gridDim.x * blockIdx.y] = tot;
     }
 }
 
-template <typename T, typename TF, bool HAS_W, int VARIANT, int TY, int COLS>
-void launch_t(const IterArgs &a, cudaStream_t s) {
-    const int sw = COLS == 1 ? SW : SW2;
+template <typename T, typename TF, bool HAS_W, int VARIANT, int TY> void launch_t(const IterArgs &a, cudaStream_t s) {
     dim3 grid = a.tiles ? dim3(a.ntiles)
-                        : dim3((a.g.W + sw - 1) / sw, (a.g.H + TY * WARPS - 1) / (TY * WARPS));
-    k_admm_roll<T, TF, HAS_W, VARIANT, TY, COLS><<<grid, dim3(32 * WARPS), 0, s>>>(a);
+                        : dim3((a.g.W + SW - 1) / SW, (a.g.H + TY * WARPS - 1) / (TY * WARPS));
+    k_admm_roll<T, TF, HAS_W, VARIANT, TY><<<grid, dim3(32 * WARPS), 0, s>>>(a);
 }
 
-template <typename T, typename TF, bool HAS_W, int VARIANT>
-void launch_ty(const IterArgs &a, int ty, int cols, cudaStream_t s) {
+template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_ty(const IterArgs &a, int ty, cudaStream_t s) {
     switch (ty) {
-    case 1: launch_t<T, TF, HAS_W, VARIANT, 1, 1>(a, s); break;
-    case 2: launch_t<T, TF, HAS_W, VARIANT, 2, 1>(a, s); break;
-    case 8:
-        if (cols == 2) launch_t<T, TF, HAS_W, VARIANT, 8, 2>(a, s);
-        else launch_t<T, TF, HAS_W, VARIANT, 8, 1>(a, s);
-        break;
-    default:
-        if (cols == 2) launch_t<T, TF, HAS_W, VARIANT, 32, 2>(a, s);
-        else launch_t<T, TF, HAS_W, VARIANT, 32, 1>(a, s);
-        break;
+    case 1: launch_t<T, TF, HAS_W, VARIANT, 1>(a, s); break;
+    case 2: launch_t<T, TF, HAS_W, VARIANT, 2>(a, s); break;
+    case 8: launch_t<T, TF, HAS_W, VARIANT, 8>(a, s); break;
+    default: launch_t<T, TF, HAS_W, VARIANT, 32>(a, s); break;
     }
 }
 
-template <typename T, typename TF> void launch_m(const IterArgs &a, int ty, int cols, cudaStream_t s) {
+template <typename T, typename TF> void launch_m(const IterArgs &a, int ty, cudaStream_t s) {
     const bool has_w = a.k.beta != 0.f;
     if (a.k.method == 1) {
         if (a.k.a_tilde_mode == 1) {
-            if (has_w) launch_ty<T, TF, true, 3>(a, ty, cols, s);
-            else launch_ty<T, TF, false, 3>(a, ty, cols, s);
+            if (has_w) launch_ty<T, TF, true, 3>(a, ty, s);
+            else launch_ty<T, TF, false, 3>(a, ty, s);
         } else {
-            if (has_w) launch_ty<T, TF, true, 1>(a, ty, cols, s);
-            else launch_ty<T, TF, false, 1>(a, ty, cols, s);
+            if (has_w) launch_ty<T, TF, true, 1>(a, ty, s);
+            else launch_ty<T, TF, false, 1>(a, ty, s);
         }
     } else {
         if (a.k.a_tilde_mode == 1) {
-            if (has_w) launch_ty<T, TF, true, 2>(a, ty, cols, s);
-            else launch_ty<T, TF, false, 2>(a, ty, cols, s);
+            if (has_w) launch_ty<T, TF, true, 2>(a, ty, s);
+            else launch_ty<T, TF, false, 2>(a, ty, s);
         } else {
-            if (has_w) launch_ty<T, TF, true, 0>(a, ty, cols, s);
-            else launch_ty<T, TF, false, 0>(a, ty, cols, s);
+            if (has_w) launch_ty<T, TF, true, 0>(a, ty, s);
+            else launch_ty<T, TF, false, 0>(a, ty, s);
         }
     }
 }

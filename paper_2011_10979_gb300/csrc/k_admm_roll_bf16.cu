@@ -4,9 +4,9 @@
 
 namespace tvl1 {
 
-void roll_launch_bf16(const IterArgs &a, int ty, int cols, bool flow32, cudaStream_t s) {
-    if (flow32) roll::launch_m<__nv_bfloat16, float>(a, ty, cols, s);
-    else roll::launch_m<__nv_bfloat16, __nv_bfloat16>(a, ty, cols, s);
+void roll_launch_bf16(const IterArgs &a, int ty, bool flow32, cudaStream_t s) {
+    if (flow32) roll::launch_m<__nv_bfloat16, float>(a, ty, s);
+    else roll::launch_m<__nv_bfloat16, __nv_bfloat16>(a, ty, s);
 }
 
 }  // namespace tvl1

@@ -3,6 +3,6 @@
 
 namespace tvl1 {
 
-void roll_launch_f32(const IterArgs &a, int ty, int cols, cudaStream_t s) { roll::launch_m<float, float>(a, ty, cols, s); }
+void roll_launch_f32(const IterArgs &a, int ty, cudaStream_t s) { roll::launch_m<float, float>(a, ty, s); }
 
 }  // namespace tvl1

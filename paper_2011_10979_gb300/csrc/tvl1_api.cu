@@ -292,8 +292,7 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
     B.key.append((const char *)&q, sizeof(q));
     if (n > 1) {
         size_t t = 0, maxpart = 1;
-        // the strip height comes from the one-column strip count; the tiles use that height's width
-        const int SWD = admm_fused_strip_w(1), NWP = admm_fused_warps();
+        const int SWD = admm_fused_strip_w(), NWP = admm_fused_warps();
         for (int l = 0; l < B.L; ++l) {
             long strip_rows = 0;
             Geom gm{0, 0, 0};
@@ -318,12 +317,12 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             gm.pitch = pitch_of(gm.W);
             B.gmax[l] = gm;
             B.tile_h[l] = admm_fused_rows_per_warp(strip_rows);
-            const int rows = B.tile_h[l] * NWP, SWT = admm_fused_strip_w(B.tile_h[l]);
+            const int rows = B.tile_h[l] * NWP;
             int nt = 0;
             for (int k = 0; k < n; ++k) {
                 if (B.res[l][k]) continue;
                 const Geom g = geom_of(B.pl[k], l);
-                nt += ((g.W + SWT - 1) / SWT) * ((g.H + rows - 1) / rows);
+                nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
             }
             B.ntiles[l] = nt;
             B.pairs_off[l][0] = t;
@@ -391,7 +390,7 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
                 P.done = p->tol > 0.0 ? &misc->done : nullptr;
                 P.tmp = (float *)(A + pl.tmp);
             }
-            const int rows = B.tile_h[l] * admm_fused_warps(), SWD = admm_fused_strip_w(B.tile_h[l]);
+            const int rows = B.tile_h[l] * admm_fused_warps(), SWD = admm_fused_strip_w();
             const int t0 = t;
             if (B.res[l][k]) rl[r++] = k;
             else sl[ns++] = k;

@@ -21,36 +21,6 @@ template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-// Two adjacent elements (off, off + 1; off even, so the pair is aligned) as one vector access.
-// The conversions round each element as the scalar forms do.
-template <typename T> struct Store2;
-template <> struct Store2<float> {
-    static __device__ __forceinline__ float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-    static __device__ __forceinline__ void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
-};
-template <> struct Store2<__half> {
-    static __device__ __forceinline__ float2 ld(const __half *p) {
-        return __half22float2(*reinterpret_cast<const __half2 *>(p));
-    }
-    static __device__ __forceinline__ void st(__half *p, float2 v) {
-        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x, v.y);
-    }
-};
-template <> struct Store2<__nv_bfloat16> {
-    static __device__ __forceinline__ float2 ld(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float2 v) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
-    }
-};
-template <typename T> __device__ __forceinline__ float2 ldT2(const void *base, size_t off) {
-    return Store2<T>::ld(reinterpret_cast<const T *>(base) + off);
-}
-template <typename T> __device__ __forceinline__ void stT2(void *base, size_t off, float2 v) {
-    Store2<T>::st(reinterpret_cast<T *>(base) + off, v);
-}
-
 // x rounded to storage type T and back: the value a store of x followed by a load yields.
 template <typename T> __device__ __forceinline__ float storage_round(float x) {
     T t;

@@ -85,14 +85,13 @@ struct IterArgs {
     const int *plist = nullptr;
 };
 
-// Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w(TY) output
+// Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w() output
 // columns and TY rows (TY = 1, 2, 8 or 32, chosen per level by admm_fused_tile_h); a block stacks
 // admm_fused_warps() strips vertically.  A work-list entry (pair, tx, ty) is the block covering
 // columns [tx * strip_w, ...) and rows [ty * warps * TY, ...).
 int admm_fused_tile_h(Geom g);
 int admm_fused_rows_per_warp(long strip_rows);   // strip_rows: sum over pairs of strips x rows
-int admm_fused_strip_w(int ty);  // output columns per strip for strip height ty
-int admm_fused_cols(int ty);     // columns per lane (1 or 2) for strip height ty
+int admm_fused_strip_w();
 int admm_fused_warps();
 
 // Level-resident engine of the ADMM methods, pDR and ALG1 (k_resident.cu): one thread-block cluster per pair keeps
