@@ -22,17 +22,15 @@ int forced_rows_per_warp() {
 }  // namespace
 
 int admm_fused_rows_per_warp(long strip_rows) {
-    // rows per warp.  Launches with ample parallelism (>= 16 warps per SM even at 32 rows:
-    // batches, very large images) take 32 (halo (32+3)/32): there bandwidth, not the chain
-    // latency, bounds the kernel and the halo re-reads matter.  Otherwise
-    // 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller levels a warp's
-    // TY + 3 row steps are the latency of the whole iteration, so there strips of two or one row
-    // trade redundant halo work for a short chain.  (Single pairs from 640x480 to 1920x1080
-    // measured fastest at 8, with 9 and 15 warps per SM at 32 rows; a 256-pair batch 5% faster
-    // at 32 than at 8.)
+    // rows per warp: 32 (halo (32+3)/32) where that still gives about eight warps per SM (large
+    // images, batches; these strips run register-capped at five blocks per SM), else 8 (halo
+    // (8+3)/8) where that gives eight warps per SM; on smaller levels a warp's TY + 3 row steps are
+    // the latency of the whole iteration, so there strips of two or one row trade redundant halo
+    // work for a short chain.  (Measured: 32 beats 8 from 1280x960 up, 31.4 vs 32.9 us per
+    // iteration at 1280x960 and 148 vs 196 us at 3840x2160; 8 wins at 640x480, 2 at 320x240.)
     if (const int f = forced_rows_per_warp()) return f;
     const long sms = 152;
-    if (strip_rows / 32 >= 16L * sms) return 32;
+    if (strip_rows / 32 >= 8L * sms) return 32;
     const int cand[3] = {8, 2, 1};
     for (int t : cand)
         if (strip_rows / t >= 8L * sms) return t;
