@@ -97,6 +97,19 @@ typedef struct {
                             ||M_s|| = max M_s, Prop. 3.1); 1 = the per-pixel diagonal
                             a~_ij = max(M_s(ij), 1e-12), which keeps c(diag(a~) - M_s) positive
                             semidefinite because M_s is diagonal (an extension, not in the paper) */
+    int rows_per_warp;   /* strip height of the fused streaming ADMM kernel (rows each warp
+                            finishes per inner iteration; the strip is 29 columns wide):
+                            0 = chosen per level from the level's size by the built-in rule;
+                            1, 2, 8 or 32 = that height on every streamed level;
+                            -1 = autotuned: the first solve of a layout on a context times every
+                            height on each streamed level (a few iterations of the real launch on
+                            the arena, after a device synchronisation) and keeps the fastest for
+                            that context.  The flow does not depend on it (the per-pixel
+                            arithmetic is the same); only the grouping of the residual's
+                            partial sums changes, so the residual (and a stopping decision
+                            taken on it) can differ in the last FP32 digits.  Used by of_solve,
+                            of_solve_batch and the serving loop; the step-level entry points
+                            use the built-in rule.                                              */
 } of_params;
 
 typedef struct {
@@ -111,7 +124,7 @@ typedef struct {
 /* Fills p with the paper's Sec. 4 settings: pADMM (r = 1), c = 0.05, a = 8, a~ = max M_s,
  * rho = 1.9, sigma = 2, tau = 0.4, beta = 0.05, one SRBGS sweep; lambda = 0.05; eta = 0.5,
  * 3 levels, 5 warps, 50 iterations; FP32, fused engine; with 16-bit storage, the last warp
- * and the flow fields in FP32. */
+ * and the flow fields in FP32; the built-in strip heights (rows_per_warp = 0). */
 void of_default_params(of_params *p);
 
 /* Creates a context on CUDA device `device`.  The context owns one device arena that grows on
@@ -132,6 +145,16 @@ size_t of_arena_bytes(int H, int W, const of_params *params);
  * kernel nodes of its CUDA graph; captures the graph if it is not cached yet).  Returns -1 on
  * error (message in of_last_error). */
 long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *params);
+
+/* Strip heights of the fused streaming ADMM kernel in a solve of n pairs of sizes H[k] x W[k]
+ * (n = 1: of_solve; n > 1: of_solve_batch) with these parameters: rows[l] for l in
+ * [0, params->levels) is the height used on pyramid level l, 0 where no pair of that level runs on
+ * the streaming ADMM kernel (a level-resident launch, pDR, ALG1, the plain engine, or a level below
+ * out_level).  With params->rows_per_warp = -1 it runs the autotuner first if this layout is not
+ * tuned on the context yet (allocating the arena and launching kernels; the device is
+ * synchronised).  `rows` is caller-owned host memory of params->levels ints.  OF_EINVAL for bad
+ * arguments, OF_ENOMEM / OF_ECUDA as for of_solve_batch. */
+of_status of_rows_per_warp(of_ctx *ctx, int n, const int *H, const int *W, const of_params *params, int *rows);
 
 /* Solves one pair (whole schedule: pyramid, levels, warps, inner iterations; Sec. 3-4).
  * I0, I1: H x W FP32 images (device, pitch `pitch`).  u, v (and w unless NULL): outputs of size

@@ -39,13 +39,13 @@ int admm_fused_rows_per_warp(long strip_rows) {
 
 int admm_fused_tile_h(Geom g) { return admm_fused_rows_per_warp((long)((g.W + roll::SW - 1) / roll::SW) * g.H); }
 
-int admm_fused_blocks(Geom g) {
-    const int th = admm_fused_tile_h(g);
+int admm_fused_blocks(Geom g, int ty) {
+    const int th = ty > 0 ? ty : admm_fused_tile_h(g);
     return ((g.W + roll::SW - 1) / roll::SW) * ((g.H + th * roll::WARPS - 1) / (th * roll::WARPS));
 }
 
 void launch_admm_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
-    const int ty = a.tiles ? a.tile_h : admm_fused_tile_h(a.g);
+    const int ty = a.tile_h > 0 ? a.tile_h : admm_fused_tile_h(a.g);
     if (prec == PREC_F32) roll_launch_f32(a, ty, s);
     else if (prec == PREC_F16) roll_launch_f16(a, ty, prec_flow == PREC_F32, s);
     else roll_launch_bf16(a, ty, prec_flow == PREC_F32, s);

@@ -177,15 +177,9 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
     return res;
 }
 
-// 32-row strips run in many waves (large images, batches): capping their registers at five
-// 128-thread blocks per SM (96 registers) raises the resident warps from 16 to 20 per SM and
-// measured 17-26% faster (a 12-16 byte spill in the beta > 0 variants included).  The shorter
-// strips keep all registers: their fully unrolled chains spill heavily under a cap.
-#ifndef ROLL_TY32_MIN_BLOCKS
-#define ROLL_TY32_MIN_BLOCKS 5
-#endif
+// The whole iteration for one block's strips (the body of both kernel entries below).
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TY>
-__global__ void __launch_bounds__(WARPS * 32, TY == 32 ? ROLL_TY32_MIN_BLOCKS : 1) k_admm_roll(IterArgs A) {
+__device__ __forceinline__ void roll_block(const IterArgs &A) {
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // ---- which strip: geometry in plain scalars, one 16-byte load per mode
@@ -249,10 +243,31 @@ __global__ void __launch_bounds__(WARPS * 32, TY == 32 ? ROLL_TY32_MIN_BLOCKS : 
     }
 }
 
+// Strips of 1, 2 and 8 rows: the compiler's own register budget for 128-thread blocks (at most 128
+// registers, four blocks per SM).  Asking for one block per SM instead let the 8-row strips take
+// 203 registers, half the resident warps, and measured 40% slower per iteration at 640x480.
+template <typename T, typename TF, bool HAS_W, int VARIANT, int TY>
+__global__ void __launch_bounds__(WARPS * 32) k_admm_roll(IterArgs A) {
+    roll_block<T, TF, HAS_W, VARIANT, TY>(A);
+}
+
+// 32-row strips run in many waves (large images, batches): capping their registers at five
+// 128-thread blocks per SM (96 registers) raises the resident warps from 16 to 20 per SM and
+// measured 17-26% faster (a 12-16 byte spill in the beta > 0 variants included).  The shorter
+// strips' fully unrolled chains spill heavily under such a cap.
+#ifndef ROLL_TY32_MIN_BLOCKS
+#define ROLL_TY32_MIN_BLOCKS 5
+#endif
+template <typename T, typename TF, bool HAS_W, int VARIANT>
+__global__ void __launch_bounds__(WARPS * 32, ROLL_TY32_MIN_BLOCKS) k_admm_roll32(IterArgs A) {
+    roll_block<T, TF, HAS_W, VARIANT, 32>(A);
+}
+
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TY> void launch_t(const IterArgs &a, cudaStream_t s) {
     dim3 grid = a.tiles ? dim3(a.ntiles)
                         : dim3((a.g.W + SW - 1) / SW, (a.g.H + TY * WARPS - 1) / (TY * WARPS));
-    k_admm_roll<T, TF, HAS_W, VARIANT, TY><<<grid, dim3(32 * WARPS), 0, s>>>(a);
+    if constexpr (TY == 32) k_admm_roll32<T, TF, HAS_W, VARIANT><<<grid, dim3(32 * WARPS), 0, s>>>(a);
+    else k_admm_roll<T, TF, HAS_W, VARIANT, TY><<<grid, dim3(32 * WARPS), 0, s>>>(a);
 }
 
 template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_ty(const IterArgs &a, int ty, cudaStream_t s) {

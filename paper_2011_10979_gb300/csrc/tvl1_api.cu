@@ -96,6 +96,9 @@ of_status validate(const of_params *p, int H, int W) {
     if (p->precision < 0 || p->precision > 2) return fail(OF_EINVAL, "unknown precision");
     if (p->engine < 0 || p->engine > 3) return fail(OF_EINVAL, "unknown engine");
     if (p->a_tilde_mode < 0 || p->a_tilde_mode > 1) return fail(OF_EINVAL, "a_tilde_mode must be 0 or 1");
+    if (p->rows_per_warp != -1 && p->rows_per_warp != 0 && p->rows_per_warp != 1 && p->rows_per_warp != 2 &&
+        p->rows_per_warp != 8 && p->rows_per_warp != 32)
+        return fail(OF_EINVAL, "rows_per_warp must be -1 (autotune), 0 (built-in rule), 1, 2, 8 or 32");
     if (p->engine == OF_ENGINE_PLAIN && p->precision != OF_PREC_FP32)
         return fail(OF_EINVAL, "the plain engine runs in FP32 only");
     if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
@@ -146,12 +149,13 @@ Plan make_plan(int H, int W, const of_params *p) {
     }
     pl.tmp = take(6 * pl.plane32);
     // partial-sum slots: the most blocks any engine launches on any level (the streaming engine's
-    // strip height changes with the level, so a coarser level can need more blocks)
+    // strip height changes with the level, so a coarser level can need more blocks; a height set
+    // in the parameters or by the autotuner can be the lowest, 1, which launches the most)
     int mb = 1;
     for (int l = 0; l < pl.L; ++l) {
         const Geom g{pl.H[l], pl.W[l], pl.P[l]};
-        mb = std::max({mb, admm_fused_blocks(g), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g),
-                       energy_blocks(g)});
+        mb = std::max({mb, admm_fused_blocks(g, p->rows_per_warp != 0 ? 1 : 0), admm_plain_blocks(g),
+                       pdr_plain_blocks(g), cp_blocks(g), energy_blocks(g)});
     }
     pl.max_blocks = mb;
     pl.partials = take(3 * (size_t)mb * sizeof(double));
@@ -179,6 +183,8 @@ struct of_ctx {
     std::map<std::string, GraphEntry> graphs;
     // the batch layout whose launch tables the arena holds (graphs of other layouts re-upload)
     std::string tables_key;
+    // autotuned strip heights of the streaming ADMM kernel, per level workload (tune_key)
+    std::map<std::string, int> tuned;
     // serving loop state (tvl1_serve.cu)
     void *server = nullptr;
 };
@@ -248,6 +254,8 @@ struct Batch {
     std::vector<Plan> pl;
     std::vector<size_t> base;
     size_t pairs_off[MAX_LEVELS][2] = {}, tiles_off[MAX_LEVELS] = {}, scal_off[MAX_LEVELS] = {};
+    // strip height of the streaming ADMM kernel per level (a single pair: 0 = the built-in rule)
+    // and, batched, the size of the level's tile work-list for it
     int ntiles[MAX_LEVELS] = {}, tile_h[MAX_LEVELS] = {};
     Geom gmax[MAX_LEVELS] = {};
     // level-resident pairs per level: flags, count, device list offset, shared memory per CTA
@@ -268,6 +276,18 @@ Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
 bool use_resident(const of_params *p, Geom g) {
     if (!admm_resident_fits(g, p->method)) return false;
     return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g, p->method));
+}
+
+// Tiles of level l's work-list (the pairs not on the level-resident engine) with strip height ty.
+int batch_tiles(const Batch &B, int l, int ty) {
+    const int rows = ty * admm_fused_warps(), SWD = admm_fused_strip_w();
+    int nt = 0;
+    for (int k = 0; k < B.n; ++k) {
+        if (B.res[l][k]) continue;
+        const Geom g = geom_of(B.pl[k], l);
+        nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
+    }
+    return nt;
 }
 
 Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
@@ -292,7 +312,7 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
     B.key.append((const char *)&q, sizeof(q));
     if (n > 1) {
         size_t t = 0, maxpart = 1;
-        const int SWD = admm_fused_strip_w(), NWP = admm_fused_warps();
+        const int SWD = admm_fused_strip_w();
         for (int l = 0; l < B.L; ++l) {
             long strip_rows = 0;
             Geom gm{0, 0, 0};
@@ -316,15 +336,11 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             }
             gm.pitch = pitch_of(gm.W);
             B.gmax[l] = gm;
-            B.tile_h[l] = admm_fused_rows_per_warp(strip_rows);
-            const int rows = B.tile_h[l] * NWP;
-            int nt = 0;
-            for (int k = 0; k < n; ++k) {
-                if (B.res[l][k]) continue;
-                const Geom g = geom_of(B.pl[k], l);
-                nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
-            }
-            B.ntiles[l] = nt;
+            B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp : admm_fused_rows_per_warp(strip_rows);
+            B.ntiles[l] = batch_tiles(B, l, B.tile_h[l]);
+            // room for the longest work-list (height 1) when the autotuner will try every height
+            const bool admm = p->method == OF_PADMM_I || p->method == OF_PADMM_II;
+            const int nt = (admm && p->rows_per_warp == -1) ? batch_tiles(B, l, 1) : B.ntiles[l];
             B.pairs_off[l][0] = t;
             t += align_up(sizeof(PairIter) * n, 256);
             B.pairs_off[l][1] = t;
@@ -345,6 +361,8 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
         off += align_up(t, 256);
         B.partials = off;
         off += align_up(maxpart * sizeof(double), 256);
+    } else {
+        for (int l = 0; l < B.L; ++l) B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp : 0;
     }
     B.total = off;
     return B;
@@ -425,8 +443,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
     const bool plain = p->engine == OF_ENGINE_PLAIN;
     const bool pingpong = !pdr && !plain;  // ADMM fused engines and ALG1 read one buffer, write the other
     const GaussTaps taps = gauss_taps(p->eta);
-    auto blocks_of = [&](Geom g) {
-        return pdr ? pdr_plain_blocks(g) : cp ? cp_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g));
+    auto blocks_of = [&](Geom g, int l) {
+        return pdr ? pdr_plain_blocks(g) : cp ? cp_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g, B.tile_h[l]));
     };
     const Coefs k = coefs_of(p);
     const int L = B.L;
@@ -586,6 +604,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     a.partials = (check || final_it) ? c.partials : nullptr;
                     a.done = p->tol > 0.0 ? &c.misc->done : nullptr;
                     a.tmp = (float *)(c.A + c.pl->tmp);
+                    a.tile_h = B.tile_h[l];
                     if (pdr) {
                         if (plain) launch_pdr_plain(a, s);
                         else launch_pdr_fused(a, prec, pflow, s);
@@ -596,7 +615,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         else launch_admm_fused(a, prec, pflow, s);
                     }
                     if (check) {
-                        const int nb = blocks_of(g);
+                        const int nb = blocks_of(g, l);
                         const double rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
                         launch_reduce_check(c.partials, nb, &c.misc->res_check, rows, p->tol, &c.misc->done,
                                             &c.misc->iters, 10, s);
@@ -650,7 +669,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     launch_reduce_check_batched(bpart, ps, n, 0.0, 0, 1, s);
                 } else {
                     const Geom g = geom_of(*pc[0].pl, l);
-                    launch_sum(pc[0].partials, blocks_of(g), &pc[0].misc->res_final, s);
+                    launch_sum(pc[0].partials, blocks_of(g, l), &pc[0].misc->res_final, s);
                 }
             }
         }
@@ -676,6 +695,130 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             }
         }
     }
+}
+
+// ------------------------------------------------------------ strip-height autotuner
+// Whether level l of layout B runs inner iterations on the streaming ADMM kernel.
+bool streamed_admm(const Batch &B, const of_params *p, int l) {
+    if (p->method != OF_PADMM_I && p->method != OF_PADMM_II) return false;
+    if (p->engine == OF_ENGINE_PLAIN || p->iters <= 0 || l < B.out_level || l >= B.L) return false;
+    return B.n > 1 ? B.ntiles[l] > 0 : !use_resident(p, geom_of(B.pl[0], l));
+}
+
+// The strip height level l runs with (streamed levels only).
+int level_rows(const Batch &B, int l) {
+    if (B.n > 1 || B.tile_h[l] > 0) return B.tile_h[l];
+    return admm_fused_tile_h(geom_of(B.pl[0], l));
+}
+
+// What the kernel's speed depends on: the kernel instance (method, per-pixel a~, beta > 0,
+// storage types), single or batched form, and the geometries of the streamed pairs.
+std::string tune_key(const Batch &B, const of_params *p, int l) {
+    const int hdr[6] = {p->method, p->a_tilde_mode, p->beta != 0.f ? 1 : 0, B.pl[0].prec, B.pl[0].pflow, B.n > 1 ? 1 : 0};
+    std::string k((const char *)hdr, sizeof(hdr));
+    for (int q = 0; q < B.n; ++q) {
+        if (B.n > 1 && B.res[l][q]) continue;
+        const Geom g = geom_of(B.pl[q], l);
+        k.append((const char *)&g.H, sizeof(int));
+        k.append((const char *)&g.W, sizeof(int));
+    }
+    return k;
+}
+
+// One inner iteration of level l on the streaming kernel, as the solve launches it (storage
+// precision of the level's main warps; no stop flag, no residual partials).
+void launch_level_iteration(of_ctx *ctx, const Batch &B, const of_params *p, int l, int parity, cudaStream_t s) {
+    IterArgs a{};
+    a.k = coefs_of(p);
+    a.tile_h = B.tile_h[l];
+    if (B.n == 1) {
+        const Plan &pl = B.pl[0];
+        char *A = ctx->arena + B.base[0];
+        const Fields b0 = fields_at(A + pl.stA, pl.planeS), b1 = fields_at(A + pl.stB, pl.planeS);
+        a.g = geom_of(pl, l);
+        a.in = parity ? b1 : b0;
+        a.out = parity ? b0 : b1;
+        a.Ix = A + pl.data;
+        a.Iy = A + pl.data + pl.planeT;
+        a.It = A + pl.data + 2 * pl.planeT;
+        a.ms_max = &((Misc *)(A + pl.misc))->ms_max;
+    } else {
+        a.pairs = (const PairIter *)(ctx->arena + B.table_off + B.pairs_off[l][0]);
+        a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
+        a.ntiles = B.ntiles[l];
+        a.parity = parity;
+    }
+    launch_admm_fused(a, B.pl[0].prec, B.pl[0].pflow, s);
+}
+
+// Times every strip height on level l (2 untimed and 6 timed iterations each, CUDA events on the
+// context's own stream) and returns the fastest; ties keep the lower height.
+of_status tune_level(of_ctx *ctx, Batch &B, const of_params *p, int l, int *best) {
+    static const int cand[4] = {1, 2, 8, 32};
+    constexpr int WARM = 2, REPS = 6;
+    of_params q = *p;
+    q.tol = 0.0;  // tables without stop flags: every timed launch does the full iteration
+    float best_ms = 0.f;
+    *best = 0;
+    for (int ty : cand) {
+        B.tile_h[l] = ty;
+        if (B.n > 1) {
+            B.ntiles[l] = batch_tiles(B, l, ty);
+            of_status st = upload_tables(ctx, B, &q);
+            if (st != OF_OK) return st;
+        }
+        for (int it = 0; it < WARM + REPS; ++it) {
+            if (it == WARM) OF_CUDA(cudaEventRecord(ctx->ev0, ctx->cap));
+            launch_level_iteration(ctx, B, &q, l, it & 1, ctx->cap);
+        }
+        OF_CUDA(cudaEventRecord(ctx->ev1, ctx->cap));
+        OF_CUDA(cudaEventSynchronize(ctx->ev1));
+        OF_CUDA(cudaGetLastError());
+        float ms = 0.f;
+        OF_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (*best == 0 || ms < best_ms) {
+            best_ms = ms;
+            *best = ty;
+        }
+    }
+    ctx->tables_key.clear();  // the arena holds the last candidate's tables
+    return OF_OK;
+}
+
+// rows_per_warp = -1: sets B's strip heights from the context's tuning, timing the levels not
+// tuned yet.  The timing launches run on the arena (state and data zeroed first; the solve
+// overwrites them) after a device synchronisation, so no queued solve still uses it.
+of_status resolve_rows(of_ctx *ctx, Batch &B, const of_params *p) {
+    if (p->rows_per_warp != -1) return OF_OK;
+    bool ready = false;
+    for (int l = B.L - 1; l >= B.out_level; --l) {
+        if (!streamed_admm(B, p, l)) continue;
+        const std::string key = tune_key(B, p, l);
+        auto it = ctx->tuned.find(key);
+        int ty = 0;
+        if (it != ctx->tuned.end()) {
+            ty = it->second;
+        } else {
+            if (!ready) {
+                OF_CUDA(cudaDeviceSynchronize());
+                for (int q = 0; q < B.n; ++q) {
+                    const Plan &pl = B.pl[q];
+                    char *A = ctx->arena + B.base[q];
+                    OF_CUDA(cudaMemsetAsync(A + pl.stA, 0, NFIELDS * pl.planeS, ctx->cap));
+                    OF_CUDA(cudaMemsetAsync(A + pl.stB, 0, NFIELDS * pl.planeS, ctx->cap));
+                    OF_CUDA(cudaMemsetAsync(A + pl.data, 0, 3 * pl.planeT, ctx->cap));
+                    OF_CUDA(cudaMemsetAsync(A + pl.misc, 0, sizeof(Misc), ctx->cap));
+                }
+                ready = true;
+            }
+            of_status st = tune_level(ctx, B, p, l, &ty);
+            if (st != OF_OK) return st;
+            ctx->tuned[key] = ty;
+        }
+        B.tile_h[l] = ty;
+        if (B.n > 1) B.ntiles[l] = batch_tiles(B, l, ty);
+    }
+    return OF_OK;
 }
 
 of_status get_graph(of_ctx *ctx, const Batch &B, const of_params *p, cudaGraphExec_t *out, cudaGraph_t *graph_out = nullptr) {
@@ -816,8 +959,9 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
     }
     if (validate(params, H, W) != OF_OK) return -1;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return -1;
-    const Batch B = make_batch(1, &H, &W, params);
+    Batch B = make_batch(1, &H, &W, params);
     if (ensure_arena(ctx, B.total) != OF_OK) return -1;
+    if (resolve_rows(ctx, B, params) != OF_OK) return -1;
     cudaGraphExec_t ge;
     cudaGraph_t g;
     if (get_graph(ctx, B, params, &ge, &g) != OF_OK) return -1;
@@ -831,6 +975,24 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
         if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
     }
     return k;
+}
+
+of_status of_rows_per_warp(of_ctx *ctx, int n, const int *H, const int *W, const of_params *params, int *rows) {
+    if (!ctx || !H || !W || !params || !rows || n < 1) return fail(OF_EINVAL, "of_rows_per_warp: NULL argument or n < 1");
+    for (int q = 0; q < n; ++q) {
+        of_status st = validate(params, H[q], W[q]);
+        if (st != OF_OK) return st;
+    }
+    OF_CUDA(cudaSetDevice(ctx->device));
+    Batch B = make_batch(n, H, W, params);
+    if (params->rows_per_warp == -1) {
+        of_status st = ensure_arena(ctx, B.total);
+        if (st != OF_OK) return st;
+        st = resolve_rows(ctx, B, params);
+        if (st != OF_OK) return st;
+    }
+    for (int l = 0; l < B.L; ++l) rows[l] = streamed_admm(B, params, l) ? level_rows(B, l) : 0;
+    return OF_OK;
 }
 
 }  // extern "C"
@@ -855,10 +1017,12 @@ of_status solve_pairs(of_ctx *ctx, int n, const float *const *I0, const float *c
         if (!host && pitch[q] < W[q]) return fail(OF_EINVAL, "pitch < W");
     }
     OF_CUDA(cudaSetDevice(ctx->device));
-    const Batch B = make_batch(n, H, W, params);
+    Batch B = make_batch(n, H, W, params);
     for (int q = 0; q < n; ++q)
         if (!host && out_pitch[q] < B.pl[q].W[B.out_level]) return fail(OF_EINVAL, "out_pitch smaller than the output width");
     of_status st = ensure_arena(ctx, B.total);
+    if (st != OF_OK) return st;
+    st = resolve_rows(ctx, B, params);
     if (st != OF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     cudaGraphExec_t ge;

@@ -76,7 +76,8 @@ struct IterArgs {
     float *tmp = nullptr;          // FP32 scratch planes (H x pitch each) for engines that need them
     // batched form (fused ADMM engine): when `tiles` is set, block b works on tiles[b] of pair
     // pairs[tiles[b].pair], reads buf[parity] and writes buf[parity ^ 1]; g/in/out/Ix/Iy/It/
-    // ms_max/done above are ignored.  tile_h is the tile height the work-list was built for.
+    // ms_max/done above are ignored.  tile_h is the tile height the work-list was built for; in
+    // the single-pair form a positive tile_h sets the strip height (0: the built-in rule).
     const PairIter *pairs = nullptr;
     const TileRef *tiles = nullptr;
     int ntiles = 0, parity = 0, tile_h = 0;
@@ -148,7 +149,9 @@ void launch_copy_planes(const void *const *src, void *const *dst, int nplanes, G
 // ---------------------------------------------------------------- ADMM (k_admm.cu)
 // Fused engine: one kernel per iteration, reads args.in, writes args.out.  The multipliers
 // (w, u, v) are stored in `prec_flow`, every other field and the linearisation data in `prec`.
-int admm_fused_blocks(Geom g);
+// Blocks of one single-pair launch with strip height ty (0: the built-in rule for g); with
+// ty = 1 the most any height launches.
+int admm_fused_blocks(Geom g, int ty = 0);
 void launch_admm_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 // Plain engine (FP32): one kernel per operator, in place on args.in; args.tmp: 3 FP32 planes.
 int admm_plain_blocks(Geom g);

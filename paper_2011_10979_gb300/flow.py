@@ -21,7 +21,7 @@ OF_PREC_FP32, OF_PREC_FP16, OF_PREC_BF16 = 0, 1, 2
 OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT = 0, 1, 2, 3
 
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
-           "of_solve_kernel_count", "of_solve",
+           "of_solve_kernel_count", "of_rows_per_warp", "of_solve",
            "of_solve_host", "of_solve_batch", "of_pyr_down", "of_upsample", "of_derivatives",
            "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_cp_iterate",
            "of_fields_bytes", "of_energy",
@@ -43,7 +43,7 @@ class of_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_last_warp", ctypes.c_int),
                 ("fp32_flow", ctypes.c_int),
                 ("engine", ctypes.c_int), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_float),
-                ("cp_sigma", ctypes.c_float), ("a_tilde_mode", ctypes.c_int)]
+                ("cp_sigma", ctypes.c_float), ("a_tilde_mode", ctypes.c_int), ("rows_per_warp", ctypes.c_int)]
 
 
 class of_stats(ctypes.Structure):
@@ -78,6 +78,7 @@ def lib():
             "of_last_error": (ctypes.c_char_p, [vp]),
             "of_arena_bytes": (sz, [i, i, P(of_params)]),
             "of_solve_kernel_count": (ctypes.c_longlong, [vp, i, i, P(of_params)]),
+            "of_rows_per_warp": (i, [vp, i, P(i), P(i), P(of_params), P(i)]),
             "of_solve": (i, [vp, vp, vp, i, i, i, P(of_params), vp, vp, vp, i, vp, P(of_stats)]),
             "of_solve_host": (i, [vp, vp, vp, i, i, P(of_params), vp, vp, vp, vp, P(of_stats)]),
             "of_solve_batch": (i, [vp, i, P(vp), P(vp), P(i), P(i), P(i), P(of_params), P(vp), P(vp), P(vp),
@@ -171,6 +172,18 @@ def of_solve_kernel_count(ctx: Context, H, W, params: of_params) -> int:
     if n < 0:
         raise OfError(OF_EINVAL, lib().of_last_error(ctx.h).decode())
     return int(n)
+
+
+def of_rows_per_warp(ctx: Context, sizes, params: of_params) -> list:
+    """Strip height of the streaming ADMM kernel per pyramid level (0 = that level does not run
+    on it) for a solve of the pairs of `sizes` [(H, W), ...]; tunes the layout first when
+    params.rows_per_warp is -1."""
+    n = len(sizes)
+    Hs = (ctypes.c_int * n)(*[int(h) for h, _ in sizes])
+    Ws = (ctypes.c_int * n)(*[int(w) for _, w in sizes])
+    rows = (ctypes.c_int * max(1, params.levels))()
+    check(lib().of_rows_per_warp(ctx.h, n, Hs, Ws, ctypes.byref(params), rows), ctx.h)
+    return list(rows)[:params.levels]
 
 
 def of_solve(ctx: Context, I0, I1, params: of_params, want_w=False, stats=True, stream=None):

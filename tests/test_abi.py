@@ -53,3 +53,21 @@ def test_arena_bytes_and_validation_without_gpu(L):
     st = L.of_solve(None, None, None, 10, 10, 10, ctypes.byref(p), None, None, None, 10, None, None)
     assert st == flow.OF_EINVAL
     assert b"ctx" in L.of_last_error(None)
+
+
+def test_rows_per_warp_validation_without_gpu(L):
+    """The strip-height field takes -1 (autotune), 0 (built-in rule) or one of the kernel's heights;
+    a set height can be the lowest, so the partial-sum slots grow to its block count."""
+    base = L.of_arena_bytes(480, 640, ctypes.byref(flow.default_params(levels=5)))
+    for ok in (-1, 0, 1, 2, 8, 32):
+        q = flow.default_params(levels=5, rows_per_warp=ok)
+        n = L.of_arena_bytes(480, 640, ctypes.byref(q))
+        assert n >= base if ok else n == base
+    for bad in (-2, 3, 4, 16, 64):
+        q = flow.default_params(levels=5, rows_per_warp=bad)
+        assert L.of_arena_bytes(480, 640, ctypes.byref(q)) == 0
+        assert b"rows_per_warp" in L.of_last_error(None)
+    rows = (ctypes.c_int * 5)()
+    H = (ctypes.c_int * 1)(480)
+    st = L.of_rows_per_warp(None, 1, H, H, ctypes.byref(flow.default_params(levels=5)), rows)
+    assert st == flow.OF_EINVAL

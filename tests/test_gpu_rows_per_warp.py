@@ -1,0 +1,134 @@
+"""Strip height of the streaming ADMM kernel (rows each warp finishes per inner iteration of
+Sec. 3.1.1's rpADMMI / rpADMMII / beta = 0 model) and its autotuner.  The height only changes how
+the work is cut into warps, so every height gives bitwise the same flow and the same iteration
+counts; only the grouping of the residual's partial sums changes (each lane adds its strip's rows
+in FP32, blocks in FP64), so the residual agrees to FP32 rounding.  Each height is also checked
+against the FP64 oracle on a level several strips wide and tall, with ragged right and bottom
+edges."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2011_10979_gb300 import flow, synth
+
+pytestmark = pytest.mark.gpu
+
+HEIGHTS = (1, 2, 8, 32)
+METHODS = {
+    "padmm": dict(method=0, r=1.0),
+    "rpadmm2": dict(method=1, rho=1.9),
+    "zach": dict(method=0, beta=0.0),
+    "padmm_pp": dict(method=0, a_tilde_mode=1),
+}
+STREAM = flow.OF_ENGINE_STREAM
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = flow.Context(0)
+    yield c
+    c.close()
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _solve(ctx, pr, **kw):
+    return flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), flow.default_params(**kw))
+
+
+@pytest.mark.parametrize("prec", [flow.OF_PREC_FP32, flow.OF_PREC_BF16])
+@pytest.mark.parametrize("name", list(METHODS))
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 200), (17, 33), (45, 61), (130, 250), (480, 640)])
+def test_every_height_gives_the_same_flow(ctx, H, W, name, prec):
+    """One level per shape on the streaming engine: a single pixel, fewer rows than one strip,
+    ragged strips and row groups, and a level 23 strips wide and 480 rows tall."""
+    pr = synth.random_affine_rect_pair(H, W, 7)
+    kw = dict(lam=2.0, levels=1, warps=2, iters=20, engine=STREAM, precision=prec, **METHODS[name])
+    u0, v0, _, s0 = _solve(ctx, pr, rows_per_warp=0, **kw)
+    for ty in HEIGHTS:
+        u, v, _, st = _solve(ctx, pr, rows_per_warp=ty, **kw)
+        assert torch.equal(u, u0) and torch.equal(v, v0), ty
+        assert st["iters_run"] == s0["iters_run"] == 40
+        assert st["residual"] == pytest.approx(s0["residual"], rel=1e-6, abs=1e-15)
+        assert st["energy"] == pytest.approx(s0["energy"], rel=1e-9, abs=1e-15)
+
+
+@pytest.mark.parametrize("ty", HEIGHTS)
+def test_every_height_vs_oracle(ctx, orc, ty):
+    """A 150 x 200 level (7 strips, ragged on the right; 150 rows, ragged for every height),
+    2 warps x 50 iterations, against the FP64 oracle at the flow tolerance of the solve tests."""
+    pr = synth.random_affine_rect_pair(150, 200, 5)
+    kw = dict(lam=5.0, levels=1, warps=2, iters=50)
+    u, v, _, st = _solve(ctx, pr, engine=STREAM, rows_per_warp=ty, **kw)
+    ru, rv, _, rst = orc.solve(pr.I0, pr.I1, orc.Params(**kw))
+    u, v = u.cpu().double().numpy(), v.cpu().double().numpy()
+    assert np.abs(u - ru).max() <= 1e-3 and np.abs(v - rv).max() <= 1e-3
+    assert np.hypot(u - ru, v - rv).mean() <= 1e-2
+    assert st["iters_run"] == rst["iters_run"]
+
+
+@pytest.mark.parametrize("tol", [0.0, 3e-3])
+def test_stopping_rule_is_height_independent(ctx, tol):
+    """With the stopping test on, every height stops each warp after the same iteration."""
+    pr = synth.random_affine_rect_pair(240, 320, 9)
+    kw = dict(lam=2.0, levels=2, warps=3, iters=60, tol=tol, engine=STREAM)
+    u0, v0, _, s0 = _solve(ctx, pr, rows_per_warp=0, **kw)
+    for ty in HEIGHTS + (-1,):
+        u, v, _, st = _solve(ctx, pr, rows_per_warp=ty, **kw)
+        assert torch.equal(u, u0) and torch.equal(v, v0), ty
+        assert st["iters_run"] == s0["iters_run"]
+
+
+@pytest.mark.parametrize("ty", HEIGHTS + (-1,))
+def test_batch_every_height_equals_single(ctx, ty):
+    """Batched work-lists built for each height (and the autotuned one) give the single-pair
+    flows bit for bit; the 1 x 1 and 64 x 48 pairs run level-resident, the others streamed."""
+    pairs = [synth.random_affine_rect_pair(240, 320, 3), synth.sinusoid_pair(seed=1),
+             synth.random_affine_rect_pair(130, 250, 4), synth.random_affine_rect_pair(436, 1024, 6),
+             synth.Pair(np.full((1, 1), 0.5, np.float32), np.full((1, 1), 0.25, np.float32), None, None)]
+    P = flow.default_params(lam=2.0, levels=3, warps=2, iters=20, rows_per_warp=ty)
+    us, vs, sts = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], P)
+    P0 = flow.default_params(lam=2.0, levels=3, warps=2, iters=20)
+    for p, u, v, st in zip(pairs, us, vs, sts):
+        su, sv, _, sst = flow.of_solve(ctx, cu(p.I0), cu(p.I1), P0)
+        assert torch.equal(u, su) and torch.equal(v, sv)
+        assert st["iters_run"] == sst["iters_run"]
+    # levels 0 and 1 stream some pairs; on level 2 every pair runs level-resident
+    rows = flow.of_rows_per_warp(ctx, [p.I0.shape for p in pairs], P)
+    assert rows[0] in HEIGHTS and rows[1] in HEIGHTS and rows[2] == 0
+    if ty > 0:
+        assert rows == [ty, ty, 0]
+
+
+def test_autotuned_single_pair(ctx):
+    """640 x 480, 5 levels, default engine: the two levels above the resident size are tuned to
+    one of the kernel's heights and the three resident levels report 0; the tuned solve equals the
+    built-in rule's bit for bit, launches as many kernels, and the tuning is kept by the context."""
+    P = flow.default_params(lam=5.0, levels=5, warps=2, iters=10, rows_per_warp=-1)
+    rows = flow.of_rows_per_warp(ctx, [(480, 640)], P)
+    assert rows[0] in HEIGHTS and rows[1] in HEIGHTS and rows[2:] == [0, 0, 0]
+    P0 = flow.default_params(lam=5.0, levels=5, warps=2, iters=10)
+    built_in = flow.of_rows_per_warp(ctx, [(480, 640)], P0)
+    assert built_in[0] in HEIGHTS and built_in[1] in HEIGHTS and built_in[2:] == [0, 0, 0]
+    pr = synth.affine_rect_pair()
+    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+    u0, v0, _, s0 = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P0)
+    assert torch.equal(u, u0) and torch.equal(v, v0)
+    assert st["iters_run"] == s0["iters_run"]
+    assert flow.of_rows_per_warp(ctx, [(480, 640)], P) == rows
+    assert flow.of_solve_kernel_count(ctx, 480, 640, P) == flow.of_solve_kernel_count(ctx, 480, 640, P0)
+
+
+def test_rows_report_for_other_kernels(ctx):
+    """Levels that do not run on the streaming ADMM kernel report 0: pDR, ALG1, the plain engine,
+    and levels below out_level."""
+    for kw in (dict(method=flow.OF_PDR), dict(method=flow.OF_CP), dict(engine=flow.OF_ENGINE_PLAIN)):
+        assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, **kw)) == [0, 0, 0]
+    rows = flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, out_level=1, rows_per_warp=8))
+    assert rows == [0, 8, 0]
+    with pytest.raises(flow.OfError):
+        flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(rows_per_warp=4))
