@@ -281,7 +281,8 @@ def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, 
     """Uneven-size batch: n pairs with sizes drawn uniformly from {96x64, 320x240, 640x480,
     1024x436, 1242x375}, affine+box motion up to 15 px (`distinct` seeded pairs, each used
     n/distinct times), BF16 storage, FP32 last warp, 5 levels x 10 warps x 100 iterations, solved
-    with of_solve_batch (one work-list launch per inner iteration for all pairs)."""
+    with of_solve_batch (one work-list launch per inner iteration for all pairs).  The streaming
+    kernel's strip height is autotuned per level on the (untimed) first solve."""
     from paper_2011_10979_gb300 import synth
     prec = flow.OF_PREC_BF16 if prec is None else prec
     base = synth.batch_pairs(n=distinct)
@@ -289,9 +290,10 @@ def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, 
     I0 = [torch.from_numpy(p.I0).to(dev) for p in pairs]
     I1 = [torch.from_numpy(p.I1).to(dev) for p in pairs]
     P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
-                            precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow)
+                            precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, rows_per_warp=-1)
     flow.of_solve_batch(flow_ctx_batch(flow, dev), I0, I1, P, stats=False)
     torch.cuda.synchronize(dev)
+    rows = flow.of_rows_per_warp(flow_ctx_batch(flow, dev), [p.I0.shape for p in pairs], P)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -306,7 +308,7 @@ def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, 
                                                         ("_duals+fp32_flow" if fp32_flow else "_all"))
     return {"workload": "%d pairs uneven sizes (%d distinct seeded pairs), pADMM, 5x10x100" % (n, distinct),
             "storage": name, "value": n / t, "unit": "flows/s",
-            "s_per_batch": t, "gpix_iter_per_s": work / 1e3 / t,
+            "rows_per_warp": {"mode": "autotuned", "per_level": rows}, "s_per_batch": t, "gpix_iter_per_s": work / 1e3 / t,
             "effective_gbs": work * 1e6 * bpp / t / 1e9, "bytes_per_px_iter": bpp}
 
 

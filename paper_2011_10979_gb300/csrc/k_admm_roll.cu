@@ -21,23 +21,26 @@ int forced_rows_per_warp() {
 }
 }  // namespace
 
-int admm_fused_rows_per_warp(long strip_rows) {
-    // rows per warp: 32 (halo (32+3)/32) where that still gives about eight warps per SM (large
-    // images, batches; these strips run register-capped at five blocks per SM), else 8 (halo
-    // (8+3)/8) where that gives eight warps per SM; on smaller levels a warp's TY + 3 row steps are
-    // the latency of the whole iteration, so there strips of two or one row trade redundant halo
-    // work for a short chain.  (Measured: 32 beats 8 from 1280x960 up, 31.4 vs 32.9 us per
-    // iteration at 1280x960 and 148 vs 196 us at 3840x2160; 8 wins at 640x480, 2 at 320x240.)
+int admm_fused_rows_per_warp(long strip_rows, bool storage16) {
+    // rows per warp: 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller
+    // levels a warp's TY + 3 row steps are the latency of the whole iteration, so there strips of
+    // two or one row trade redundant halo work for a short chain.  With 16-bit storage, launches of
+    // at least 16 warps per SM even at 32 rows (batches, very large images) take 32 (halo
+    // (32+3)/32, the register-capped kernel).  Measured per iteration (FP32, single pairs): 320x240
+    // 4.1 us at 2 rows; 640x480 8.4-8.6 at 2 or 8; 1280x960 24.3 at 8 vs 31.6 at 32; 3840x2160
+    // 143 vs 149; a 64-pair batch 288 vs 304 in FP32 but 331 vs 285 with BF16 duals.
     if (const int f = forced_rows_per_warp()) return f;
     const long sms = 152;
-    if (strip_rows / 32 >= 8L * sms) return 32;
+    if (storage16 && strip_rows / 32 >= 16L * sms) return 32;
     const int cand[3] = {8, 2, 1};
     for (int t : cand)
         if (strip_rows / t >= 8L * sms) return t;
     return 1;
 }
 
-int admm_fused_tile_h(Geom g) { return admm_fused_rows_per_warp((long)((g.W + roll::SW - 1) / roll::SW) * g.H); }
+int admm_fused_tile_h(Geom g, bool storage16) {
+    return admm_fused_rows_per_warp((long)((g.W + roll::SW - 1) / roll::SW) * g.H, storage16);
+}
 
 int admm_fused_blocks(Geom g, int ty) {
     const int th = ty > 0 ? ty : admm_fused_tile_h(g);

@@ -336,7 +336,8 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             }
             gm.pitch = pitch_of(gm.W);
             B.gmax[l] = gm;
-            B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp : admm_fused_rows_per_warp(strip_rows);
+            B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp
+                                               : admm_fused_rows_per_warp(strip_rows, p->precision != OF_PREC_FP32);
             B.ntiles[l] = batch_tiles(B, l, B.tile_h[l]);
             // room for the longest work-list (height 1) when the autotuner will try every height
             const bool admm = p->method == OF_PADMM_I || p->method == OF_PADMM_II;
@@ -362,7 +363,10 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
         B.partials = off;
         off += align_up(maxpart * sizeof(double), 256);
     } else {
-        for (int l = 0; l < B.L; ++l) B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp : 0;
+        for (int l = 0; l < B.L; ++l)
+            B.tile_h[l] = p->rows_per_warp > 0    ? p->rows_per_warp
+                          : p->rows_per_warp == 0 ? admm_fused_tile_h(geom_of(B.pl[0], l), p->precision != OF_PREC_FP32)
+                                                  : 0;  // set by the autotuner
     }
     B.total = off;
     return B;
@@ -708,7 +712,7 @@ bool streamed_admm(const Batch &B, const of_params *p, int l) {
 // The strip height level l runs with (streamed levels only).
 int level_rows(const Batch &B, int l) {
     if (B.n > 1 || B.tile_h[l] > 0) return B.tile_h[l];
-    return admm_fused_tile_h(geom_of(B.pl[0], l));
+    return admm_fused_tile_h(geom_of(B.pl[0], l), B.pl[0].prec != PREC_F32);
 }
 
 // What the kernel's speed depends on: the kernel instance (method, per-pixel a~, beta > 0,

@@ -90,8 +90,10 @@ struct IterArgs {
 // columns and TY rows (TY = 1, 2, 8 or 32, chosen per level by admm_fused_tile_h); a block stacks
 // admm_fused_warps() strips vertically.  A work-list entry (pair, tx, ty) is the block covering
 // columns [tx * strip_w, ...) and rows [ty * warps * TY, ...).
-int admm_fused_tile_h(Geom g);
-int admm_fused_rows_per_warp(long strip_rows);   // strip_rows: sum over pairs of strips x rows
+// The built-in rule; storage16: the duals are stored in 16 bits.  The FP32 rule never takes a
+// greater height than the 16-bit one, so admm_fused_blocks(g) bounds the blocks of both.
+int admm_fused_tile_h(Geom g, bool storage16 = false);
+int admm_fused_rows_per_warp(long strip_rows, bool storage16 = false);   // strip_rows: sum over pairs of strips x rows
 int admm_fused_strip_w();
 int admm_fused_warps();
 
