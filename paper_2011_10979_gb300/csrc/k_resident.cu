@@ -822,23 +822,41 @@ int admm_resident_max_clusters() {
     return m;
 }
 
-size_t admm_resident_smem(Geom g, int method) {
-    const int nc = admm_resident_cluster();
+size_t admm_resident_smem(Geom g, int method, int nc) {
+    if (nc <= 0) nc = admm_resident_cluster();
     const size_t rpc = (size_t)((g.H + nc - 1) / nc);
     return (rpc + 2) * (size_t)g.W * (method == 2 ? NPL_PDR : NPL) * sizeof(float);
 }
 
 bool admm_resident_fits(Geom g, int method) {
-    return g.H >= 1 && g.W >= 1 && admm_resident_smem(g, method) <= SMEM_MAX;
+    return g.H >= 1 && g.W >= 1 && admm_resident_smem(g, method, 0) <= SMEM_MAX;
+}
+
+namespace {
+// TVL1_RESIDENT_CLUSTER=1|2|4|8|16 pins the cluster size wherever the level fits (read once; for
+// tuning sweeps).
+int forced_cluster() {
+    static const int v = [] {
+        const char *e = getenv("TVL1_RESIDENT_CLUSTER");
+        const int t = e ? atoi(e) : 0;
+        return (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) ? t : 0;
+    }();
+    return v;
+}
+}  // namespace
+
+int admm_resident_nc(Geom g, int method) {
+    const int f = forced_cluster();
+    if (f && f <= admm_resident_cluster() && admm_resident_smem(g, method, f) <= SMEM_MAX) return f;
+    return admm_resident_cluster();
 }
 
 // pDR's per-kernel engine takes 2n + 3 launches per iteration, so its resident form wins at every
 // size that fits; the ADMM methods and ALG1 (one launch per iteration) only up to RESIDENT_MAX_PX.
 bool admm_resident_preferred(Geom g, int method) { return method == 2 || (long)g.H * g.W <= RESIDENT_MAX_PX; }
 
-cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, size_t smem, int prec, int prec_flow,
+cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, int nc, size_t smem, int prec, int prec_flow,
                                  cudaStream_t s) {
-    const int nc = admm_resident_cluster();
     if (prec == PREC_F32) return launch_m<float, float>(a, nclusters, nc, smem, s);
     if (prec == PREC_F16)
         return prec_flow == PREC_F32 ? launch_m<__half, float>(a, nclusters, nc, smem, s)

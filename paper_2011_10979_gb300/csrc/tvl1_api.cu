@@ -262,6 +262,7 @@ struct Batch {
     std::vector<char> res[MAX_LEVELS];
     int nres[MAX_LEVELS] = {};
     size_t reslist_off[MAX_LEVELS] = {}, res_smem[MAX_LEVELS] = {};
+    int res_nc[MAX_LEVELS] = {};  // CTAs per cluster of the level's resident launch
     // the other pairs, for the one-slice-per-pair batched kernels (ALG1)
     size_t streamlist_off[MAX_LEVELS] = {};
     size_t partials = 0, table_off = 0, table_bytes = 0, total = 0;
@@ -329,11 +330,16 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
                 if (take && use_resident(p, g)) {
                     B.res[l][k] = 1;
                     ++B.nres[l];
-                    B.res_smem[l] = std::max(B.res_smem[l], admm_resident_smem(g, p->method));
+                    B.res_nc[l] = std::max(B.res_nc[l], admm_resident_nc(g, p->method));
                     continue;
                 }
                 strip_rows += (long)((g.W + SWD - 1) / SWD) * g.H;
             }
+            // one cluster size for the launch: the largest any of its pairs asks for (a larger
+            // cluster only shrinks a pair's band)
+            for (int k = 0; k < n; ++k)
+                if (B.res[l][k])
+                    B.res_smem[l] = std::max(B.res_smem[l], admm_resident_smem(geom_of(B.pl[k], l), p->method, B.res_nc[l]));
             gm.pitch = pitch_of(gm.W);
             B.gmax[l] = gm;
             B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp
@@ -577,12 +583,13 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     r.sc.iters = &c.misc->iters;
                     r.sc.rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
                     r.sc.resident = 1;
-                    launch_admm_resident(r, 1, admm_resident_smem(g, p->method), prec, pflow, s);
+                    const int nc = admm_resident_nc(g, p->method);
+                    launch_admm_resident(r, 1, nc, admm_resident_smem(g, p->method, nc), prec, pflow, s);
                 } else {
                     r.pairs = (const PairIter *)(ctx->arena + B.table_off + B.pairs_off[l][in32 ? 1 : 0]);
                     r.scal = (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]);
                     r.list = (const int *)(ctx->arena + B.table_off + B.reslist_off[l]);
-                    launch_admm_resident(r, B.nres[l], B.res_smem[l], prec, pflow, s);
+                    launch_admm_resident(r, B.nres[l], B.res_nc[l], B.res_smem[l], prec, pflow, s);
                 }
             }
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),

@@ -120,10 +120,13 @@ struct ResArgs {
 };
 int admm_resident_cluster();           // CTAs per cluster: 16 where the device schedules it, else 8
 int admm_resident_max_clusters();      // resident clusters that run at once (one CTA per SM)
-size_t admm_resident_smem(Geom g, int method);  // dynamic shared memory of one CTA for this level
+// dynamic shared memory of one CTA for this level in a cluster of nc CTAs (0: the largest cluster)
+size_t admm_resident_smem(Geom g, int method, int nc);
 bool admm_resident_fits(Geom g, int method);    // whether a level of this geometry fits one cluster
+int admm_resident_nc(Geom g, int method);       // the cluster size a level of this geometry runs with
 bool admm_resident_preferred(Geom g, int method);  // whether the resident launch is the faster engine
-cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, size_t smem, int prec, int prec_flow,
+// nclusters clusters of nc CTAs (one per pair), each with smem bytes of dynamic shared memory
+cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, int nc, size_t smem, int prec, int prec_flow,
                                  cudaStream_t s);
 
 // ---------------------------------------------------------------- pyramid / warp (k_pyramid.cu)
