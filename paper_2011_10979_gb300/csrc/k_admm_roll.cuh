@@ -74,12 +74,10 @@ __device__ __forceinline__ void load_row(Row &R, const void *const *src, int i, 
 // sum of squared constraint residuals of its output pixels (FP32; the block sum is FP64).
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TY, bool INT>
 __device__ __forceinline__ float strip(const void *const *src, void *const *dst, int H, int W, int P, int c0, int y0,
-                                       int lane, const Coefs &K, float at) {
+                                       int lane, const Coefs &K, const float *msp) {
     const int c = c0 + lane;                   // this lane's column
     const bool out_lane = lane >= 2 && lane < 2 + SW && (INT || c < W);
     const bool ex = INT || c < W - 1, wx = INT || c > 0;   // east / west neighbour inside the image
-    const StepK SK = step_coefs(K, at);
-
     // rows i-1 (prev) and i (cur) in registers, rows i+1 (n1) and i+2 (n2) in flight
     constexpr int NROWS = TY + 3;
     constexpr int UNROLL = TY <= 8 ? NROWS : 4;
@@ -92,6 +90,9 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
 
     load_row<T, TF, HAS_W, INT>(n1, src, y0 - 2, c, H, W, P);
     load_row<T, TF, HAS_W, INT>(n2, src, y0 - 1, c, H, W, P);
+    // a~ (one device scalar of the warp) and the step coefficients after the first rows' loads
+    // are in flight, so their latencies overlap
+    const StepK SK = step_coefs(K, a_tilde_of(K, msp));
 #pragma unroll UNROLL
     for (int k = 0; k < NROWS; ++k) {
         const int i = y0 - 2 + k;                 // row entering the window
@@ -227,16 +228,14 @@ __device__ __forceinline__ void roll_block(const IterArgs &A) {
             src[9] = A.It;
         }
     }
-    const int stopped = donep ? *donep : 0;
-    const float at = a_tilde_of(A.k, msp);
-    if (stopped) return;  // uniform per block: the pair's warp met its stopping test
+    if (donep && *donep) return;  // uniform per block: the pair's warp met its stopping test
 
     const int c0 = sx * SW - 2;                // first column of the strip
     const int y0 = sy * TY;                    // first output row of the strip
     // interior strip: columns c0 .. c0+31 and rows y0-2 .. y0+TY all away from the image border
     const bool interior = c0 >= 1 && c0 + 32 <= W - 1 && y0 >= 2 && y0 + TY <= H - 2;
-    const float res = interior ? strip<T, TF, HAS_W, VARIANT, TY, true>(src, dst, H, W, P, c0, y0, lane, A.k, at)
-                               : strip<T, TF, HAS_W, VARIANT, TY, false>(src, dst, H, W, P, c0, y0, lane, A.k, at);
+    const float res = interior ? strip<T, TF, HAS_W, VARIANT, TY, true>(src, dst, H, W, P, c0, y0, lane, A.k, msp)
+                               : strip<T, TF, HAS_W, VARIANT, TY, false>(src, dst, H, W, P, c0, y0, lane, A.k, msp);
     if (A.partials) {
         const double tot = block_sum((double)res, red);
         if (threadIdx.x == 0) A.partials[blockIdx.x + gridDim.x * blockIdx.y] = tot;
