@@ -151,6 +151,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch16(args):
+    """The batch leg alone on 16 uneven pairs (BF16 duals + FP32 flow, autotuned strip heights),
+    one timed batch: a short command for profiling the batched kernels.  Streaming engine on every
+    level, as in the 256-pair batch, where no level has few enough small pairs for the
+    level-resident launch."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2011_10979_gb300 import flow
+    from paper_2011_10979_gb300.build import build
+    build()
+    r = batch_measure(flow, torch, dev, n=16, distinct=16, fp32_flow=1, steps=1, engine=flow.OF_ENGINE_STREAM,
+                      rows_per_warp=args.rows_per_warp)
+    print(json.dumps({"legs": "batch16", "batch": r}))
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -277,12 +293,14 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, steps=2):
+def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, steps=2, engine=None,
+                  rows_per_warp=-1):
     """Uneven-size batch: n pairs with sizes drawn uniformly from {96x64, 320x240, 640x480,
     1024x436, 1242x375}, affine+box motion up to 15 px (`distinct` seeded pairs, each used
     n/distinct times), BF16 storage, FP32 last warp, 5 levels x 10 warps x 100 iterations, solved
     with of_solve_batch (one work-list launch per inner iteration for all pairs).  The streaming
-    kernel's strip height is autotuned per level on the (untimed) first solve."""
+    kernel's strip height is autotuned per level on the (untimed) first solve unless rows_per_warp
+    sets it."""
     from paper_2011_10979_gb300 import synth
     prec = flow.OF_PREC_BF16 if prec is None else prec
     base = synth.batch_pairs(n=distinct)
@@ -290,7 +308,8 @@ def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, 
     I0 = [torch.from_numpy(p.I0).to(dev) for p in pairs]
     I1 = [torch.from_numpy(p.I1).to(dev) for p in pairs]
     P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
-                            precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, rows_per_warp=-1)
+                            precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, rows_per_warp=rows_per_warp,
+                            engine=flow.OF_ENGINE_FUSED if engine is None else engine)
     flow.of_solve_batch(flow_ctx_batch(flow, dev), I0, I1, P, stats=False)
     torch.cuda.synchronize(dev)
     rows = flow.of_rows_per_warp(flow_ctx_batch(flow, dev), [p.I0.shape for p in pairs], P)
@@ -308,7 +327,8 @@ def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, 
                                                         ("_duals+fp32_flow" if fp32_flow else "_all"))
     return {"workload": "%d pairs uneven sizes (%d distinct seeded pairs), pADMM, 5x10x100" % (n, distinct),
             "storage": name, "value": n / t, "unit": "flows/s",
-            "rows_per_warp": {"mode": "autotuned", "per_level": rows}, "s_per_batch": t, "gpix_iter_per_s": work / 1e3 / t,
+            "rows_per_warp": {"mode": "autotuned" if P.rows_per_warp == -1 else "set", "per_level": rows},
+            "s_per_batch": t, "gpix_iter_per_s": work / 1e3 / t,
             "effective_gbs": work * 1e6 * bpp / t / 1e9, "bytes_per_px_iter": bpp}
 
 
@@ -510,12 +530,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     # "solve": only the timed single-pair solve (and its e2e leg), e.g. as a short command to run
-    # under a profiler; "all" (default) adds the roofline, plain, batch, serving, precision, solver
-    # and CPU-baseline legs
-    ap.add_argument("--legs", default="all", choices=["all", "solve"])
+    # under a profiler; "batch16": only a 16-pair batch (one GPU), likewise; "all" (default) adds the
+    # roofline, plain, batch, serving, precision, solver and CPU-baseline legs
+    ap.add_argument("--legs", default="all", choices=["all", "solve", "batch16"])
+    # strip height of the batch16 leg (-1: autotuned; a fixed height makes the launch sequence
+    # independent of timing, e.g. under a profiler)
+    ap.add_argument("--rows-per-warp", type=int, default=-1, choices=[-1, 0, 1, 2, 8, 32])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.legs == "batch16":
+        run_batch16(args)
     else:
         run_ours(args)
 
