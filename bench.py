@@ -152,8 +152,9 @@ def run_reference(args):
 
 
 def run_batch16(args):
-    """The batch leg alone on 16 uneven pairs (BF16 duals + FP32 flow, autotuned strip heights),
-    one timed batch: a short command for profiling the batched kernels.  Streaming engine on every
+    """The batch leg alone on 16 uneven pairs (BF16 duals + FP32 flow, strip heights autotuned
+    unless --rows-per-warp sets one), one timed batch: a short command for profiling the batched
+    kernels.  Streaming engine on every
     level, as in the 256-pair batch, where no level has few enough small pairs for the
     level-resident launch."""
     import torch
