@@ -71,3 +71,32 @@ def test_rows_per_warp_validation_without_gpu(L):
     H = (ctypes.c_int * 1)(480)
     st = L.of_rows_per_warp(None, 1, H, H, ctypes.byref(flow.default_params(levels=5)), rows)
     assert st == flow.OF_EINVAL
+
+
+def _golden_params():
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "sec4_parameters.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                name, value = line.split()[:2]
+                out[name] = float(value)
+    return out
+
+
+def test_defaults_match_the_printed_sec4_settings(L):
+    """The library's defaults and each method's settings against the values Sec. 4 prints
+    (tests/golden/sec4_parameters.txt).  ALG1's primal step reads the garbled rule as
+    1 / (L^2 tau)."""
+    g = _golden_params()
+    p = flow.default_params()
+    assert p.c == pytest.approx(g["c"]) and p.r == pytest.approx(g["r_padmm"])
+    assert p.rho == pytest.approx(g["rho_rpadmm2"])
+    assert p.sigma == pytest.approx(g["pdr_sigma"]) and p.tau == pytest.approx(g["pdr_tau"])
+    assert p.cp_tau == pytest.approx(g["alg1_tau"])
+    assert p.cp_sigma == pytest.approx(1.0 / (g["alg1_L2"] * g["alg1_tau"]))
+    assert p.beta == pytest.approx(g["beta"]) and p.a == pytest.approx(g["a"])
+    # rpADMMI's printed relaxation lies inside the range the library accepts, (0, (1 + sqrt 5) / 2)
+    q = flow.default_params(levels=5, r=g["r_rpadmm1"])
+    assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
+    q = flow.default_params(levels=5, beta=g["beta_alt"])
+    assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
