@@ -769,6 +769,7 @@ of_status tune_level(of_ctx *ctx, Batch &B, const of_params *p, int l, int *best
     constexpr int WARM = 2, REPS = 6;
     of_params q = *p;
     q.tol = 0.0;  // tables without stop flags: every timed launch does the full iteration
+    ctx->tables_key.clear();  // from here on the arena's tables are the candidates' (also on error)
     float best_ms = 0.f;
     *best = 0;
     for (int ty : cand) {
@@ -776,6 +777,7 @@ of_status tune_level(of_ctx *ctx, Batch &B, const of_params *p, int l, int *best
         if (B.n > 1) {
             B.ntiles[l] = batch_tiles(B, l, ty);
             of_status st = upload_tables(ctx, B, &q);
+            ctx->tables_key.clear();
             if (st != OF_OK) return st;
         }
         for (int it = 0; it < WARM + REPS; ++it) {
@@ -792,7 +794,6 @@ of_status tune_level(of_ctx *ctx, Batch &B, const of_params *p, int l, int *best
             *best = ty;
         }
     }
-    ctx->tables_key.clear();  // the arena holds the last candidate's tables
     return OF_OK;
 }
 
