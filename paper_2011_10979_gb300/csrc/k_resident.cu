@@ -851,7 +851,7 @@ int admm_resident_nc(Geom g, int method) {
     return admm_resident_cluster();
 }
 
-// pDR's per-kernel engine takes 2n + 3 launches per iteration, so its resident form wins at every
+// pDR's per-kernel engine takes 2n + 1 launches per iteration, so its resident form wins at every
 // size that fits; the ADMM methods and ALG1 (one launch per iteration) only up to RESIDENT_MAX_PX.
 bool admm_resident_preferred(Geom g, int method) { return method == 2 || (long)g.H * g.W <= RESIDENT_MAX_PX; }
 
