@@ -189,7 +189,7 @@ BATCH_SIZES = ((64, 96), (240, 320), (480, 640), (436, 1024), (375, 1242))   # (
 
 def batch_pairs(n=256, seed=3, max_motion=15.0):
     """Uneven-size batch: sizes drawn uniformly from BATCH_SIZES, each pair an affine+box pair
-    with its own seed and a random motion of at most max_motion px."""
+    with its own seed (random_affine_rect_pair)."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
@@ -199,6 +199,12 @@ def batch_pairs(n=256, seed=3, max_motion=15.0):
 
 
 def random_affine_rect_pair(H, W, seed, max_motion=15.0, sigma=0.01):
+    """Affine+box pair with random parameters: translation up to max_motion / 2 px, rotation up
+    to 2 degrees and zoom 0.98 .. 1.03 about the image centre, and a box of up to 120 x 80 px
+    (a quarter of the image at most) moving by 0.3 .. 1 x max_motion px.  The box motion and the
+    translation stay within max_motion; rotation and zoom add up to about 0.05 px per px of
+    distance from the centre, so the corners of the largest images move up to about 1.5 x
+    max_motion."""
     rng = np.random.default_rng(seed)
     rot = float(rng.uniform(-2.0, 2.0))
     zoom = float(rng.uniform(0.98, 1.03))
