@@ -17,10 +17,18 @@ Parity status per function (the pins live in ``tests/test_oracle_*.py``):
                           same certified minimum)
   cp_step (ALG1) ........ pinned (dual step = projection, primal step = prox optimality,
                           same certified minimum as ADMM at a fixed linearisation)
-  pyramid / upsample .... pinned only by exactness properties (constants, ramps, ratios)
-  warp_linearise ........ pinned by identities (zero flow, integer shifts, rho(d0) = I1w - I0)
-  solve (end to end) .... pinned by known-flow recovery; absolute values otherwise
-                          parity unpinned (the paper's data sets are not available)
+  gauss_smooth .......... pinned (scipy.ndimage.gaussian_filter1d with half-sample reflection,
+                          impulse responses at the border and inside)
+  downsample / upsample . pinned (that smoothing, then scipy.ndimage.map_coordinates at the
+                          pixel centres; constants, ramps, size ratios)
+  derivatives ........... pinned (numpy.gradient inside, halved one-sided differences at the border)
+  warp_linearise ........ pinned (map_coordinates at the displaced positions; identities)
+  solve (schedule) ...... pinned (a 1 x 1 pair solved by hand for every method across levels and
+                          warps; a two-level pair equal to the composition of the pinned steps,
+                          with planted schedule mistakes shown to fail; out_level = a one-level
+                          solve of the downsampled pair; known-flow recovery).  The absolute
+                          flow values on the paper's own sequences stay unpinned (the data sets
+                          are not available).
 """
 from __future__ import annotations
 
