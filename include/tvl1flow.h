@@ -41,7 +41,9 @@ typedef enum {
     OF_ENOMEM = 2,    /* the device arena would exceed the context's HBM budget, or cudaMalloc failed */
     OF_ECUDA = 3,     /* a CUDA runtime call failed (message names it) */
     OF_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
-    OF_ENUMERIC = 5,  /* non-finite residual or energy (NaN/Inf input or parameters) */
+    OF_ENUMERIC = 5,  /* non-finite residual or energy (NaN/Inf input or parameters); reported
+                         by the calls that wait for the solve (a stats pointer given, or a
+                         `_host` entry point); the other calls return after enqueueing */
     OF_EBUSY = 6      /* the serving loop is not running / queue full */
 } of_status;
 
@@ -156,6 +158,16 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
  * arguments, OF_ENOMEM / OF_ECUDA as for of_solve_batch. */
 of_status of_rows_per_warp(of_ctx *ctx, int n, const int *H, const int *W, const of_params *params, int *rows);
 
+/* Capacity of the level-resident engine on the current CUDA device: *cluster_ctas receives the
+ * CTAs per thread-block cluster it launches (16, or 8 where the device cannot schedule 16 CTAs
+ * with a full band of shared memory, or 0 when it can schedule neither, which turns the engine
+ * off: every level then runs on the streaming kernels), *max_active how many such clusters the
+ * device runs at once (cudaOccupancyMaxActiveClusters, which follows the GPC layout and can be
+ * fewer than SMs / cluster_ctas).  A batch runs a level's small pairs on the resident engine only
+ * when they fit in one such wave of clusters; otherwise they join the streaming work-list.
+ * Queried once per process.  OF_EINVAL for NULL pointers. */
+of_status of_resident_clusters(int *cluster_ctas, int *max_active);
+
 /* Solves one pair (whole schedule: pyramid, levels, warps, inner iterations; Sec. 3-4).
  * I0, I1: H x W FP32 images (device, pitch `pitch`).  u, v (and w unless NULL): outputs of size
  * H_l x W_l at level params->out_level, FP32, pitch `out_pitch` (>= W_l).  stats: optional; if
@@ -235,7 +247,9 @@ of_status of_admm_iterate(of_fields f, const float *Ix, const float *Iy, const f
  * library holds it until the process exits), so fields with of_fields_bytes(H, pitch) > 32 MiB
  * are rejected with OF_EINVAL (640 x 480 FP32 fits).  The caller still passes every field and
  * the linearisation data.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.  It calls
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.  The
+ * cached address belongs to the device's primary context (the CUDA runtime's): a cudaDeviceReset
+ * after the first call, or a different current context, is not supported.  It calls
  * no cudaMalloc/cudaFree.  All calls on a device share its one array, which keeps the last call's
  * contents; each call clears what must start at zero, but two calls that overlap on the same GPU
  * (e.g. issued on different streams) race on it: serialise them.  Arguments, results and errors

@@ -1,25 +1,11 @@
 // k_admm_roll.cu -- launch policy of the row-streaming ADMM kernel (k_admm_roll.cuh): strip
 // height per level and storage-type dispatch.
-#include <stdlib.h>
-
 #include "k_admm_roll.cuh"
 
 namespace tvl1 {
 
 int admm_fused_strip_w() { return roll::SW; }
 int admm_fused_warps() { return roll::WARPS; }
-
-namespace {
-// TVL1_ADMM_ROWS_PER_WARP=1|2|8|32 pins the strip height (read once; for tuning sweeps).
-int forced_rows_per_warp() {
-    static const int v = [] {
-        const char *e = getenv("TVL1_ADMM_ROWS_PER_WARP");
-        const int t = e ? atoi(e) : 0;
-        return (t == 1 || t == 2 || t == 8 || t == 32) ? t : 0;
-    }();
-    return v;
-}
-}  // namespace
 
 int admm_fused_rows_per_warp(long strip_rows, bool storage16) {
     // rows per warp: 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller
@@ -29,7 +15,6 @@ int admm_fused_rows_per_warp(long strip_rows, bool storage16) {
     // (32+3)/32, the register-capped kernel).  Measured per iteration (FP32, single pairs): 320x240
     // 4.1 us at 2 rows; 640x480 8.4-8.6 at 2 or 8; 1280x960 24.3 at 8 vs 31.6 at 32; 3840x2160
     // 143 vs 149; a 64-pair batch 288 vs 304 in FP32 but 331 vs 285 with BF16 duals.
-    if (const int f = forced_rows_per_warp()) return f;
     const long sms = 152;
     if (storage16 && strip_rows / 32 >= 16L * sms) return 32;
     const int cand[3] = {8, 2, 1};

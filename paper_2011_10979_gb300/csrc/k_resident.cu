@@ -29,7 +29,7 @@
 // decision.  The per-pixel arithmetic is that of the streaming engine (k_admm_math.cuh).
 #include <cooperative_groups.h>
 #include <math.h>
-#include <stdlib.h>
+#include <stdint.h>
 
 #include <type_traits>
 
@@ -734,16 +734,28 @@ __global__ void __launch_bounds__(RT, 1) k_pdr_resident(ResArgs A) {
     cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
+constexpr size_t SMEM_MAX = 200 * 1024;  // dynamic shared memory a CTA may use for its band
+
+// The function attributes every launch of one kernel instance needs, set once per instance and
+// process: the dynamic shared-memory ceiling at SMEM_MAX (not at one launch's own size -- a
+// CUDA graph node captured with a larger band than a later launch would otherwise find the
+// function's ceiling lowered beneath it) and, for 16-CTA clusters, the non-portable size.
+template <typename K> cudaError_t prepare_kernel(K kern) {
+    static const cudaError_t e = [kern] {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
+        if (r == cudaSuccess) r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        return r;
+    }();
+    return e;
+}
+
 template <typename K>
 cudaError_t launch_cluster(K kern, const ResArgs &a, int nclusters, int nc, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > SMEM_MAX || nclusters < 1 || nc < 1) return cudaErrorInvalidValue;
+    cudaError_t e = prepare_kernel(kern);
     if (e != cudaSuccess) return e;
-    if (nc > 8) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nclusters * nc);
+    cfg.gridDim = dim3(nclusters * nc);   // a whole number of clusters
     cfg.blockDim = dim3(RT);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -767,36 +779,58 @@ cudaError_t launch_m(const ResArgs &a, int nclusters, int nc, size_t smem, cudaS
     return has_w ? go(k_admm_resident<T, TF, true, 0>) : go(k_admm_resident<T, TF, false, 0>);
 }
 
-constexpr size_t SMEM_MAX = 200 * 1024;  // dynamic shared memory a CTA may use for its band
+// The cluster size and how many such clusters the device runs at once, for a launch with a full
+// band of shared memory (one CTA per SM): 16 CTAs (a non-portable size) where the device
+// schedules at least one such cluster, else 8, else none (the resident engine is then off).
+// cudaOccupancyMaxActiveClusters counts what the GPC layout allows, which is fewer than
+// SMs / cluster size when a GPC cannot hold a whole 16-CTA cluster.  Queried once, with one
+// instance of the kernels: every instance launches 512 threads with at most 128 registers and a
+// band of up to SMEM_MAX bytes, so all share the same one-CTA-per-SM occupancy.
+struct ClusterCaps {
+    int nc = 0, active = 0;
+};
 
-// The largest cluster the device schedules with a full band of shared memory: 16 CTAs (a
-// non-portable size) where available, else 8.  Queried once.
-int query_cluster() {
+ClusterCaps query_cluster() {
+    ClusterCaps c;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 8;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return c;
+    }
     auto kern = k_admm_resident<float, float, true, 0>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX) != cudaSuccess ||
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    if (prepare_kernel(kern) != cudaSuccess) {
         cudaGetLastError();
-        return 8;
+        return c;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(RT);
-    cfg.dynamicSmemBytes = SMEM_MAX;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 16;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 8;
+    for (int nc : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nc);
+        cfg.blockDim = dim3(RT);
+        cfg.dynamicSmemBytes = SMEM_MAX;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = nc;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        if (n > 0) {
+            c.nc = nc;
+            c.active = n;
+            return c;
+        }
     }
-    return n > 0 ? 16 : 8;
+    return c;
+}
+
+const ClusterCaps &cluster_caps() {
+    static const ClusterCaps c = query_cluster();
+    return c;
 }
 
 // Largest level (pixels) the default engine runs resident: above it one cluster's 16 SMs
@@ -805,51 +839,22 @@ constexpr long RESIDENT_MAX_PX = 32000;
 
 }  // namespace
 
-int admm_resident_cluster() {
-    static const int nc = query_cluster();
-    return nc;
-}
+int admm_resident_cluster() { return cluster_caps().nc; }
 
-int admm_resident_max_clusters() {
-    static const int m = [] {
-        int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-            cudaGetLastError();
-            return 1;
-        }
-        return sms / admm_resident_cluster() > 0 ? sms / admm_resident_cluster() : 1;
-    }();
-    return m;
-}
+int admm_resident_max_clusters() { return cluster_caps().active; }
 
 size_t admm_resident_smem(Geom g, int method, int nc) {
     if (nc <= 0) nc = admm_resident_cluster();
+    if (nc <= 0) return SIZE_MAX;
     const size_t rpc = (size_t)((g.H + nc - 1) / nc);
     return (rpc + 2) * (size_t)g.W * (method == 2 ? NPL_PDR : NPL) * sizeof(float);
 }
 
 bool admm_resident_fits(Geom g, int method) {
-    return g.H >= 1 && g.W >= 1 && admm_resident_smem(g, method, 0) <= SMEM_MAX;
+    return admm_resident_cluster() > 0 && g.H >= 1 && g.W >= 1 && admm_resident_smem(g, method, 0) <= SMEM_MAX;
 }
 
-namespace {
-// TVL1_RESIDENT_CLUSTER=1|2|4|8|16 pins the cluster size wherever the level fits (read once; for
-// tuning sweeps).
-int forced_cluster() {
-    static const int v = [] {
-        const char *e = getenv("TVL1_RESIDENT_CLUSTER");
-        const int t = e ? atoi(e) : 0;
-        return (t == 1 || t == 2 || t == 4 || t == 8 || t == 16) ? t : 0;
-    }();
-    return v;
-}
-}  // namespace
-
-int admm_resident_nc(Geom g, int method) {
-    const int f = forced_cluster();
-    if (f && f <= admm_resident_cluster() && admm_resident_smem(g, method, f) <= SMEM_MAX) return f;
-    return admm_resident_cluster();
-}
+int admm_resident_nc(Geom, int) { return admm_resident_cluster(); }
 
 // pDR's per-kernel engine takes 2n + 1 launches per iteration, so its resident form wins at every
 // size that fits; the ADMM methods and ALG1 (one launch per iteration) only up to RESIDENT_MAX_PX.

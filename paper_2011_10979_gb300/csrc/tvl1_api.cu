@@ -989,6 +989,14 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
     return k;
 }
 
+of_status of_resident_clusters(int *cluster_ctas, int *max_active) {
+    if (!cluster_ctas || !max_active) return fail(OF_EINVAL, "of_resident_clusters: NULL pointer");
+    *cluster_ctas = admm_resident_cluster();
+    *max_active = admm_resident_max_clusters();
+    OF_CUDA(cudaGetLastError());
+    return OF_OK;
+}
+
 of_status of_rows_per_warp(of_ctx *ctx, int n, const int *H, const int *W, const of_params *params, int *rows) {
     if (!ctx || !H || !W || !params || !rows || n < 1) return fail(OF_EINVAL, "of_rows_per_warp: NULL argument or n < 1");
     for (int q = 0; q < n; ++q) {
@@ -1064,12 +1072,16 @@ of_status solve_pairs(of_ctx *ctx, int n, const float *const *I0, const float *c
                 OF_CUDA(cudaMemcpy2DAsync(dst[k], dp, out + k * on, (size_t)pl.P[lo] * 4, (size_t)pl.W[lo] * 4,
                                           pl.H[lo], kout, s));
     }
-    if (stats) {
+    // a call that waits for the solve anyway (stats requested, or the host entry point) also
+    // checks the FP64 residual and energy for non-finite values
+    if (stats || sync) {
         float ms = 0.f;
         for (int q = 0; q < n; ++q) {
-            st = read_stats(ctx, B, q, params, s, stats + q);
-            if (q == 0) cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-            stats[q].ms = ms;
+            of_stats local;
+            of_stats *out = stats ? stats + q : &local;
+            st = read_stats(ctx, B, q, params, s, out);
+            if (stats && q == 0) cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            out->ms = ms;
             if (st != OF_OK) return st;
         }
     }
@@ -1156,12 +1168,28 @@ of_status of_warp_linearise(const float *I0, const float *I1, const float *I1x, 
     return OF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Partial-sum slots of the step-level scratch for an H-row plane set of pitch `pitch`: the most
+// blocks any engine launches at any width W <= pitch.  Every engine's block count grows with W,
+// and the fused ADMM kernel launches the most blocks with 1-row strips, whatever strip height the
+// built-in rule picks for the actual width.
+int fields_partial_slots(int H, int pitch) {
+    const Geom g{H, pitch, pitch};
+    return std::max({admm_fused_blocks(g, 1), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g)});
+}
+
+}  // namespace
+
+extern "C" {
+
 size_t of_fields_bytes(int H, int pitch) {
     if (H < 1 || pitch < 1) return 0;
     const size_t plane = align_up((size_t)H * pitch * 4, 256);
-    Geom g{H, pitch, pitch};
-    const int mb = std::max({admm_fused_blocks(g), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g)});
-    return (NFIELDS + 6) * plane + align_up((size_t)mb * sizeof(double), 256) + align_up(sizeof(Misc), 256);
+    return (NFIELDS + 6) * plane + align_up((size_t)fields_partial_slots(H, pitch) * sizeof(double), 256) +
+           align_up(sizeof(Misc), 256);
 }
 
 namespace {
@@ -1204,7 +1232,13 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
     for (int k = 0; k < NFIELDS; ++k)
         if (!user.f[k]) user.f[k] = other.f[k];
     float *tmp = (float *)(S + NFIELDS * plane);
-    const int mb = std::max({admm_fused_blocks(g), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g)});
+    // the scratch layout depends on (H, pitch) only, as of_fields_bytes does; the engine in use
+    // must find room for its partial sums in it
+    const int mb = fields_partial_slots(H, pitch);
+    const int nb_used = pdr ? pdr_plain_blocks(g)
+                            : cp ? cp_blocks(g)
+                                 : (params->engine == OF_ENGINE_PLAIN ? admm_plain_blocks(g) : admm_fused_blocks(g));
+    if (nb_used > mb) return fail(OF_EINVAL, "internal: partial sums exceed the scratch layout");
     double *partials = (double *)(S + (NFIELDS + 6) * plane);
     Misc *misc = (Misc *)(S + (NFIELDS + 6) * plane + align_up((size_t)mb * sizeof(double), 256));
     OF_CUDA(cudaMemsetAsync(misc, 0, sizeof(Misc), s));

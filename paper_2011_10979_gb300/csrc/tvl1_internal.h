@@ -118,8 +118,8 @@ struct ResArgs {
     int iters = 0, check = 0, final_res = 0;
     double tol = 0.0;
 };
-int admm_resident_cluster();           // CTAs per cluster: 16 where the device schedules it, else 8
-int admm_resident_max_clusters();      // resident clusters that run at once (one CTA per SM)
+int admm_resident_cluster();           // CTAs per cluster: 16 where the device schedules it, else 8, else 0 (off)
+int admm_resident_max_clusters();      // such clusters the device runs at once (cudaOccupancyMaxActiveClusters)
 // dynamic shared memory of one CTA for this level in a cluster of nc CTAs (0: the largest cluster)
 size_t admm_resident_smem(Geom g, int method, int nc);
 bool admm_resident_fits(Geom g, int method);    // whether a level of this geometry fits one cluster

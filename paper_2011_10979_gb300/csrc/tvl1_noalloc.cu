@@ -21,7 +21,9 @@ constexpr int MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // In host code `g_noalloc_scratch` names a host-side stand-in, not device memory: its device
-// address is looked up once per device (with that device current) and cached here.
+// address is looked up once per device (with that device current) and cached here.  The cache
+// assumes the device's primary context, which the CUDA runtime uses, and no cudaDeviceReset
+// between calls (a reset unloads the module and so the array).
 std::mutex g_mu;
 void *g_scratch_ptr[MAX_DEVICES] = {};
 
@@ -44,9 +46,15 @@ extern "C" of_status of_admm_iterate_noalloc(of_fields f, const float *Ix, const
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+    if (e != cudaSuccess) {
         tvl1_set_error(("of_admm_iterate_noalloc: cudaGetDevice: " + std::string(cudaGetErrorString(e))).c_str());
         return OF_ECUDA;
+    }
+    if (dev < 0 || dev >= MAX_DEVICES) {
+        tvl1_set_error(("of_admm_iterate_noalloc: device " + std::to_string(dev) + " is beyond the " +
+                        std::to_string(MAX_DEVICES) + " devices this entry point keeps an address for")
+                           .c_str());
+        return OF_EINVAL;
     }
     void *scratch = nullptr;
     {

@@ -21,7 +21,7 @@ OF_PREC_FP32, OF_PREC_FP16, OF_PREC_BF16 = 0, 1, 2
 OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT = 0, 1, 2, 3
 
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
-           "of_solve_kernel_count", "of_rows_per_warp", "of_solve",
+           "of_solve_kernel_count", "of_rows_per_warp", "of_resident_clusters", "of_solve",
            "of_solve_host", "of_solve_batch", "of_pyr_down", "of_upsample", "of_derivatives",
            "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_cp_iterate",
            "of_fields_bytes", "of_energy",
@@ -79,6 +79,7 @@ def lib():
             "of_arena_bytes": (sz, [i, i, P(of_params)]),
             "of_solve_kernel_count": (ctypes.c_longlong, [vp, i, i, P(of_params)]),
             "of_rows_per_warp": (i, [vp, i, P(i), P(i), P(of_params), P(i)]),
+            "of_resident_clusters": (i, [P(i), P(i)]),
             "of_solve": (i, [vp, vp, vp, i, i, i, P(of_params), vp, vp, vp, i, vp, P(of_stats)]),
             "of_solve_host": (i, [vp, vp, vp, i, i, P(of_params), vp, vp, vp, vp, P(of_stats)]),
             "of_solve_batch": (i, [vp, i, P(vp), P(vp), P(i), P(i), P(i), P(of_params), P(vp), P(vp), P(vp),
@@ -184,6 +185,13 @@ def of_rows_per_warp(ctx: Context, sizes, params: of_params) -> list:
     rows = (ctypes.c_int * max(1, params.levels))()
     check(lib().of_rows_per_warp(ctx.h, n, Hs, Ws, ctypes.byref(params), rows), ctx.h)
     return list(rows)[:params.levels]
+
+
+def of_resident_clusters() -> tuple:
+    """(CTAs per cluster, clusters the device runs at once) of the level-resident engine."""
+    nc, act = ctypes.c_int(0), ctypes.c_int(0)
+    check(lib().of_resident_clusters(ctypes.byref(nc), ctypes.byref(act)))
+    return nc.value, act.value
 
 
 def of_solve(ctx: Context, I0, I1, params: of_params, want_w=False, stats=True, stream=None):

