@@ -64,8 +64,15 @@ typedef enum {
                                inner iteration.  Both give bitwise the same flow. */
     OF_ENGINE_PLAIN = 1,    /* one kernel per operator, FP32 only: the plain reference GPU path */
     OF_ENGINE_STREAM = 2,   /* the fused streaming kernel on every level */
-    OF_ENGINE_RESIDENT = 3  /* the level-resident launch on every level that fits one cluster's
+    OF_ENGINE_RESIDENT = 3, /* the level-resident launch on every level that fits one cluster's
                                shared memory, the streaming kernel on the others */
+    OF_ENGINE_PERSISTENT = 4 /* ADMM methods: levels that the default engine does not run
+                               level-resident run every inner iteration of a warp in one
+                               persistent launch over all pairs of the level, whose warps
+                               synchronise with their neighbours through device counters
+                               (bounded waits: OF_ETIMEOUT if one runs out); pDR and ALG1 as
+                               OF_ENGINE_FUSED.  Bitwise the same flow as the other fused
+                               engines. */
 } of_engine;
 
 /* Solver parameters.  Defaults (of_default_params) are the paper's Sec. 4 settings. */
@@ -167,6 +174,17 @@ of_status of_rows_per_warp(of_ctx *ctx, int n, const int *H, const int *W, const
  * when they fit in one such wave of clusters; otherwise they join the streaming work-list.
  * Queried once per process.  OF_EINVAL for NULL pointers. */
 of_status of_resident_clusters(int *cluster_ctas, int *max_active);
+
+/* Self-test of the bounded device-side waits of the persistent engine (OF_ENGINE_PERSISTENT):
+ * runs `iters` pADMM iterations of that engine on zero-filled fields of one H x W level (it
+ * allocates and frees its own device buffers, on the current device and the legacy stream),
+ * with segment `withhold` of the launch never publishing its progress (-1: none) and every wait
+ * bounded by wait_ms milliseconds.  *timed_out receives 1 when a wait ran out -- the launch then
+ * ended early with its error flag set, and the device stays usable -- else 0.  *segments
+ * (optional) receives the launch's segment count.  OF_EINVAL for bad arguments, OF_ECUDA when a
+ * CUDA call fails. */
+of_status of_persistent_selftest(int H, int W, int iters, int withhold, double wait_ms, int *timed_out,
+                                 int *segments);
 
 /* Solves one pair (whole schedule: pyramid, levels, warps, inner iterations; Sec. 3-4).
  * I0, I1: H x W FP32 images (device, pitch `pitch`).  u, v (and w unless NULL): outputs of size

@@ -69,18 +69,28 @@ __device__ __forceinline__ void load_row(Row &R, const void *const *src, int i, 
     R.v = ok ? ldT<TF>(src[12], o) : 0.f;
 }
 
-// One warp's strip: TY output rows of the 29 output columns starting at c0 + 2.  INT: the strip and
-// its halo lie strictly inside the image, so every boundary test folds away.  Returns this lane's
-// sum of squared constraint residuals of its output pixels (FP32; the block sum is FP64).
+#ifndef ROLL_RUNTIME_UNROLL  // unroll of the run-time row loop: the four-row register rotation
+#define ROLL_RUNTIME_UNROLL 4
+#endif
+
+// One warp's strip: TY output rows of the 29 output columns starting at c0 + 2 (TY = 0: `ny` rows,
+// a run-time count).  INT: the strip and its halo lie strictly inside the image, so every boundary
+// test folds away.  skp: the warp's step coefficients when the caller has them already (else they
+// are formed here, after the first rows' loads are in flight).  Returns this lane's sum of squared
+// constraint residuals of its output pixels (FP32; the block or warp sum is FP64).
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TY, bool INT>
 __device__ __forceinline__ float strip(const void *const *src, void *const *dst, int H, int W, int P, int c0, int y0,
-                                       int lane, const Coefs &K, const float *msp) {
+                                       int lane, const Coefs &K, const float *msp, int ny = 0,
+                                       const StepK *skp = nullptr) {
     const int c = c0 + lane;                   // this lane's column
     const bool out_lane = lane >= 2 && lane < 2 + SW && (INT || c < W);
     const bool ex = INT || c < W - 1, wx = INT || c > 0;   // east / west neighbour inside the image
-    // rows i-1 (prev) and i (cur) in registers, rows i+1 (n1) and i+2 (n2) in flight
-    constexpr int NROWS = TY + 3;
-    constexpr int UNROLL = TY <= 8 ? NROWS : 4;
+    // rows i-1 (prev) and i (cur) in registers, rows i+1 (n1) and i+2 (n2) in flight.  A run-time
+    // row count unrolls by the four-row register rotation only (a short loop body that stays in
+    // the instruction cache).
+    const int ty = TY > 0 ? TY : ny;
+    const int NROWS = ty + 3;
+    constexpr int UNROLL = TY == 0 ? ROLL_RUNTIME_UNROLL : (TY <= 8 ? TY + 3 : 4);
     Row prev{}, cur{}, n1{}, n2{};
     float dp_prev = 0.f, dq1_prev = 0.f, dq2_prev = 0.f;   // div y^k on row i-1
     float six_prev = 0.f, siy_prev = 0.f;                  // (s Ix, s Iy) on row i-1
@@ -92,7 +102,7 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
     load_row<T, TF, HAS_W, INT>(n2, src, y0 - 1, c, H, W, P);
     // a~ (one device scalar of the warp) and the step coefficients after the first rows' loads
     // are in flight, so their latencies overlap
-    const StepK SK = step_coefs(K, a_tilde_of(K, msp));
+    const StepK SK = skp ? *skp : step_coefs(K, a_tilde_of(K, msp));
 #pragma unroll UNROLL
     for (int k = 0; k < NROWS; ++k) {
         const int i = y0 - 2 + k;                 // row entering the window
@@ -144,7 +154,7 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
         // ---- finish row i-1: div y^{k+1}, s, multipliers, residual, stores
         const float np1W = __shfl_up_sync(FULL, np1, 1), nq11W = __shfl_up_sync(FULL, nq11, 1);
         const float nq21W = __shfl_up_sync(FULL, nq21, 1);
-        if (pin && out_lane && im >= y0 && im < y0 + TY) {
+        if (pin && out_lane && im >= y0 && im < y0 + ty) {
             const bool nyy = INT || im > 0;
             float dpn = 0.f;
             if (HAS_W) dpn = div2(ex ? np1 : 0.f, wx ? np1W : 0.f, hy ? np2 : 0.f, nyy ? yp2_n : 0.f);

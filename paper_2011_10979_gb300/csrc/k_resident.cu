@@ -31,6 +31,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "k_admm_math.cuh"
@@ -739,14 +741,18 @@ constexpr size_t SMEM_MAX = 200 * 1024;  // dynamic shared memory a CTA may use 
 // The function attributes every launch of one kernel instance needs, set once per instance and
 // process: the dynamic shared-memory ceiling at SMEM_MAX (not at one launch's own size -- a
 // CUDA graph node captured with a larger band than a later launch would otherwise find the
-// function's ceiling lowered beneath it) and, for 16-CTA clusters, the non-portable size.
+// function's ceiling lowered beneath it) and, for 16-CTA clusters, the non-portable size.  All
+// instances share one function-pointer type, so the record is keyed by the pointer itself.
 template <typename K> cudaError_t prepare_kernel(K kern) {
-    static const cudaError_t e = [kern] {
-        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
-        if (r == cudaSuccess) r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        return r;
-    }();
-    return e;
+    static std::mutex mu;
+    static std::map<const void *, cudaError_t> done;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = done.find((const void *)kern);
+    if (it != done.end()) return it->second;
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_MAX);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    done[(const void *)kern] = r;
+    return r;
 }
 
 template <typename K>

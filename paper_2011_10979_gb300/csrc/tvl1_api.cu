@@ -63,6 +63,7 @@ struct Misc {
     int done;
     long long iters;
     double res_check, res_final, energy, dual;
+    int timeout;  // a bounded wait of the persistent engine ran out
 };
 
 of_status validate(const of_params *p, int H, int W) {
@@ -94,7 +95,7 @@ of_status validate(const of_params *p, int H, int W) {
     if (p->iters < 0) return fail(OF_EINVAL, "iters must be >= 0");
     if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(OF_EINVAL, "tol must be >= 0");
     if (p->precision < 0 || p->precision > 2) return fail(OF_EINVAL, "unknown precision");
-    if (p->engine < 0 || p->engine > 3) return fail(OF_EINVAL, "unknown engine");
+    if (p->engine < 0 || p->engine > 4) return fail(OF_EINVAL, "unknown engine");
     if (p->a_tilde_mode < 0 || p->a_tilde_mode > 1) return fail(OF_EINVAL, "a_tilde_mode must be 0 or 1");
     if (p->rows_per_warp != -1 && p->rows_per_warp != 0 && p->rows_per_warp != 1 && p->rows_per_warp != 2 &&
         p->rows_per_warp != 8 && p->rows_per_warp != 32)
@@ -266,6 +267,14 @@ struct Batch {
     // the other pairs, for the one-slice-per-pair batched kernels (ALG1)
     size_t streamlist_off[MAX_LEVELS] = {};
     size_t partials = 0, table_off = 0, table_bytes = 0, total = 0;
+    // persistent ADMM engine per level (any n): the segment plan and the offsets (in the table
+    // region) of its segments, warp lists, per-pair scalars, counters and partial sums
+    bool pers[MAX_LEVELS] = {};
+    std::vector<PSeg> psegs[MAX_LEVELS];
+    std::vector<int> pwoff[MAX_LEVELS], pwseg[MAX_LEVELS], pbegin[MAX_LEVELS], pend[MAX_LEVELS];
+    int pnwarps[MAX_LEVELS] = {};
+    size_t pseg_off[MAX_LEVELS] = {}, pwoff_off[MAX_LEVELS] = {}, pwseg_off[MAX_LEVELS] = {},
+           pscal_off[MAX_LEVELS] = {}, pctr_off[MAX_LEVELS] = {}, ppart_off[MAX_LEVELS] = {};
     std::string key;
 };
 
@@ -276,7 +285,8 @@ Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
 // launch to beat the per-iteration kernels (all methods have a resident form).
 bool use_resident(const of_params *p, Geom g) {
     if (!admm_resident_fits(g, p->method)) return false;
-    return p->engine == OF_ENGINE_RESIDENT || (p->engine == OF_ENGINE_FUSED && admm_resident_preferred(g, p->method));
+    return p->engine == OF_ENGINE_RESIDENT ||
+           ((p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_PERSISTENT) && admm_resident_preferred(g, p->method));
 }
 
 // Tiles of level l's work-list (the pairs not on the level-resident engine) with strip height ty.
@@ -289,6 +299,102 @@ int batch_tiles(const Batch &B, int l, int ty) {
         nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
     }
     return nt;
+}
+
+// Segments of one level for the persistent engine.  gs: per pair its level geometry, H = 0 for a
+// pair that is not on the engine at this level; max_warps: the warps one wave of the launch holds.
+// Every segment gets about the same number of rows (at least two, unless its pair has fewer than
+// four); a single pair is cut into as many segments as there are warps, a batch into segments of
+// the batch's mean rows per warp.  When there are more segments than warps, each goes, longest
+// first, to the warp with the fewest rows so far.
+struct PersistPlan {
+    std::vector<PSeg> segs;
+    std::vector<int> woff, wseg, pbegin, pend;
+    int nwarps = 0;
+};
+
+PersistPlan plan_persist(const std::vector<Geom> &gs, int max_warps) {
+    PersistPlan pp;
+    const int n = (int)gs.size(), SWD = admm_fused_strip_w();
+    pp.pbegin.assign(n, 0);
+    pp.pend.assign(n, 0);
+    double R = 0.0;
+    int active = 0;
+    for (const Geom &g : gs)
+        if (g.H > 0) {
+            R += (double)((g.W + SWD - 1) / SWD) * g.H;
+            ++active;
+        }
+    if (active == 0 || max_warps < 1) return pp;
+    const double L = std::max(2.0, R / max_warps);  // rows per segment
+    auto rows_of = [&](const PSeg &sg) {
+        const int h = gs[sg.pair].H;
+        return (int)((long long)(sg.t + 1) * h / sg.m - (long long)sg.t * h / sg.m);
+    };
+    for (int k = 0; k < n; ++k) {
+        const Geom g = gs[k];
+        pp.pbegin[k] = (int)pp.segs.size();
+        if (g.H > 0) {
+            const int S = (g.W + SWD - 1) / SWD;
+            int m = active == 1 ? max_warps / S : (int)std::lround(g.H / L);
+            m = std::max(1, std::min(m, std::max(1, g.H / 2)));
+            for (int t = 0; t < m; ++t)
+                for (int sx = 0; sx < S; ++sx) pp.segs.push_back(PSeg{k, sx, t, m});
+        }
+        pp.pend[k] = (int)pp.segs.size();
+    }
+    const int N = (int)pp.segs.size();
+    std::vector<std::vector<int>> lists;
+    if (N <= max_warps) {
+        lists.resize(N);
+        for (int q = 0; q < N; ++q) lists[q].push_back(q);
+    } else {
+        lists.resize(max_warps);
+        std::vector<int> order(N);
+        for (int q = 0; q < N; ++q) order[q] = q;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return rows_of(pp.segs[a]) > rows_of(pp.segs[b]); });
+        std::vector<std::pair<long long, int>> heap;  // (rows so far, warp), min-heap
+        for (int w = 0; w < max_warps; ++w) heap.push_back({0, w});
+        auto cmp = [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) { return a > b; };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (int q : order) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto &top = heap.back();
+            lists[top.second].push_back(q);
+            top.first += rows_of(pp.segs[q]) + 3;   // a segment's row steps: its rows and the halo
+            std::push_heap(heap.begin(), heap.end(), cmp);
+        }
+        for (auto &l : lists) std::sort(l.begin(), l.end());
+    }
+    pp.nwarps = (int)lists.size();
+    pp.woff.push_back(0);
+    for (auto &l : lists) {
+        for (int q : l) pp.wseg.push_back(q);
+        pp.woff.push_back((int)pp.wseg.size());
+    }
+    return pp;
+}
+
+// Whether level l of this layout runs its inner iterations on the persistent engine (ADMM
+// methods, engine OF_ENGINE_PERSISTENT, a pair left to the per-iteration kernels).
+bool pers_level(const Batch &B, const of_params *p, int l) {
+    if (p->engine != OF_ENGINE_PERSISTENT || p->iters < 1) return false;
+    if (p->method != OF_PADMM_I && p->method != OF_PADMM_II) return false;
+    if (l < B.out_level) return false;
+    for (int k = 0; k < B.n; ++k)
+        if (B.n > 1 ? !B.res[l][k] : !use_resident(p, geom_of(B.pl[0], l))) return true;
+    return false;
+}
+
+// Warps one wave of the persistent launch holds for this layout's kernel instances (the FP32
+// instance too where the finest level's last warp switches to FP32 storage).
+int persist_warps(const Batch &B, const of_params *p) {
+    const Coefs k = coefs_of(p);
+    int cap = persist_capacity(k, B.pl[0].prec, B.pl[0].pflow);
+    if (B.pl[0].use32_last) cap = std::min(cap, persist_capacity(k, PREC_F32, PREC_F32));
+    if (cap <= 0) cap = 152 * 3;  // no device to ask (sizing only): a full GB300
+    return cap * admm_fused_warps();
 }
 
 Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
@@ -363,16 +469,63 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             const size_t np = std::max({(size_t)nt, (size_t)n * pdr_plain_blocks(gm), (size_t)n * cp_blocks(gm)});
             maxpart = std::max(maxpart, np);
         }
-        B.table_off = off;
         B.table_bytes = t;
-        off += align_up(t, 256);
-        B.partials = off;
-        off += align_up(maxpart * sizeof(double), 256);
+        B.partials = maxpart;  // slots for now; an offset once the tables are laid out
     } else {
         for (int l = 0; l < B.L; ++l)
             B.tile_h[l] = p->rows_per_warp > 0    ? p->rows_per_warp
                           : p->rows_per_warp == 0 ? admm_fused_tile_h(geom_of(B.pl[0], l), p->precision != OF_PREC_FP32)
                                                   : 0;  // set by the autotuner
+    }
+    // persistent engine tables (any n; a single pair also needs its PairIter descriptors)
+    size_t t = B.table_bytes;
+    int maxw = 0;
+    for (int l = 0; l < B.L; ++l) {
+        B.pers[l] = pers_level(B, p, l);
+        if (!B.pers[l]) continue;
+        if (maxw == 0) maxw = persist_warps(B, p);
+        std::vector<Geom> gs(n);
+        for (int k = 0; k < n; ++k) {
+            const Geom g = geom_of(B.pl[k], l);
+            const bool on = n > 1 ? !B.res[l][k] : !use_resident(p, g);
+            gs[k] = on ? g : Geom{0, 0, 0};
+        }
+        PersistPlan pp = plan_persist(gs, maxw);
+        const size_t N = pp.segs.size();
+        if (n == 1) {
+            B.pairs_off[l][0] = t;
+            t += align_up(sizeof(PairIter), 256);
+            B.pairs_off[l][1] = t;
+            t += align_up(sizeof(PairIter), 256);
+        }
+        B.pseg_off[l] = t;
+        t += align_up(sizeof(PSeg) * N, 256);
+        B.pwoff_off[l] = t;
+        t += align_up(sizeof(int) * (pp.nwarps + 1), 256);
+        B.pwseg_off[l] = t;
+        t += align_up(sizeof(int) * N, 256);
+        B.pscal_off[l] = t;
+        t += align_up(sizeof(PairScalars) * n, 256);
+        B.pctr_off[l] = t;
+        t += align_up(sizeof(unsigned) * (N + n), 256);
+        B.ppart_off[l] = t;
+        t += align_up(sizeof(double) * N, 256);
+        B.psegs[l] = std::move(pp.segs);
+        B.pwoff[l] = std::move(pp.woff);
+        B.pwseg[l] = std::move(pp.wseg);
+        B.pbegin[l] = std::move(pp.pbegin);
+        B.pend[l] = std::move(pp.pend);
+        B.pnwarps[l] = pp.nwarps;
+    }
+    B.table_bytes = t;
+    if (t > 0) {
+        B.table_off = off;
+        off += align_up(t, 256);
+    }
+    if (n > 1) {
+        const size_t maxpart = B.partials;
+        B.partials = off;
+        off += align_up(maxpart * sizeof(double), 256);
     }
     B.total = off;
     return B;
@@ -380,11 +533,47 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
 
 // Writes the batched-launch tables (absolute device pointers into the current arena).
 of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
-    if (B.n <= 1) return OF_OK;
+    if (B.table_bytes == 0) return OF_OK;
     std::vector<char> img(B.table_bytes, 0);
     const bool pdr = p->method == OF_PDR, cp = p->method == OF_CP;
     const bool xb = pdr || cp;  // one grid slice per pair (pDR, ALG1) instead of a tile work-list
-    for (int l = 0; l < B.L; ++l) {
+    // the descriptors of pair k at level l, for its storage-precision and its FP32 buffers
+    auto pair_iter = [&](PairIter *pi0, PairIter *pi1, int k, int l) {
+        const Plan &pl = B.pl[k];
+        char *A = ctx->arena + B.base[k];
+        Misc *misc = (Misc *)(A + pl.misc);
+        for (int v = 0; v < 2; ++v) {
+            PairIter &P = v ? pi1[k] : pi0[k];
+            P.g = geom_of(pl, l);
+            if (v == 0) {
+                P.buf[0] = fields_at(A + pl.stA, pl.planeS);
+                P.buf[1] = fields_at(A + pl.stB, pl.planeS);
+                P.Ix = A + pl.data;
+                P.Iy = A + pl.data + pl.planeT;
+                P.It = A + pl.data + 2 * pl.planeT;
+            } else {
+                P.buf[0] = fields_at(A + pl.stA32, pl.plane32);
+                P.buf[1] = fields_at(A + pl.stB32, pl.plane32);
+                P.Ix = A + pl.data32;
+                P.Iy = A + pl.data32 + pl.plane32;
+                P.It = A + pl.data32 + 2 * pl.plane32;
+            }
+            P.ms_max = &misc->ms_max;
+            P.done = p->tol > 0.0 ? &misc->done : nullptr;
+            P.tmp = (float *)(A + pl.tmp);
+        }
+    };
+    auto scalars = [&](PairScalars &ps, int k, int l) {
+        Misc *misc = (Misc *)(ctx->arena + B.base[k] + B.pl[k].misc);
+        const Geom g = geom_of(B.pl[k], l);
+        ps.res_check = &misc->res_check;
+        ps.res_final = &misc->res_final;
+        ps.done = &misc->done;
+        ps.iters = &misc->iters;
+        ps.rows = (double)g.H * g.W * (p->beta != 0.f ? 3.0 : 2.0);
+        ps.timeout = &misc->timeout;
+    };
+    for (int l = 0; l < B.L && B.n > 1; ++l) {
         PairIter *pi0 = (PairIter *)(img.data() + B.pairs_off[l][0]);
         PairIter *pi1 = (PairIter *)(img.data() + B.pairs_off[l][1]);
         TileRef *tr = (TileRef *)(img.data() + B.tiles_off[l]);
@@ -394,30 +583,8 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
         int t = 0, r = 0, ns = 0;
         const int G = cp ? cp_blocks(B.gmax[l]) : pdr_plain_blocks(B.gmax[l]);
         for (int k = 0; k < B.n; ++k) {
-            const Plan &pl = B.pl[k];
-            char *A = ctx->arena + B.base[k];
-            Misc *misc = (Misc *)(A + pl.misc);
-            const Geom g = geom_of(pl, l);
-            for (int v = 0; v < 2; ++v) {
-                PairIter &P = v ? pi1[k] : pi0[k];
-                P.g = g;
-                if (v == 0) {
-                    P.buf[0] = fields_at(A + pl.stA, pl.planeS);
-                    P.buf[1] = fields_at(A + pl.stB, pl.planeS);
-                    P.Ix = A + pl.data;
-                    P.Iy = A + pl.data + pl.planeT;
-                    P.It = A + pl.data + 2 * pl.planeT;
-                } else {
-                    P.buf[0] = fields_at(A + pl.stA32, pl.plane32);
-                    P.buf[1] = fields_at(A + pl.stB32, pl.plane32);
-                    P.Ix = A + pl.data32;
-                    P.Iy = A + pl.data32 + pl.plane32;
-                    P.It = A + pl.data32 + 2 * pl.plane32;
-                }
-                P.ms_max = &misc->ms_max;
-                P.done = p->tol > 0.0 ? &misc->done : nullptr;
-                P.tmp = (float *)(A + pl.tmp);
-            }
+            const Geom g = geom_of(B.pl[k], l);
+            pair_iter(pi0, pi1, k, l);
             const int rows = B.tile_h[l] * admm_fused_warps(), SWD = admm_fused_strip_w();
             const int t0 = t;
             if (B.res[l][k]) rl[r++] = k;
@@ -425,14 +592,26 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
             if (!B.res[l][k])
                 for (int ty = 0; ty < (g.H + rows - 1) / rows; ++ty)
                     for (int tx = 0; tx < (g.W + SWD - 1) / SWD; ++tx) tr[t++] = TileRef{k, tx, ty, 0};
-            ps[k].res_check = &misc->res_check;
-            ps[k].res_final = &misc->res_final;
-            ps[k].done = &misc->done;
-            ps[k].iters = &misc->iters;
-            ps[k].rows = (double)g.H * g.W * (p->beta != 0.f ? 3.0 : 2.0);
+            scalars(ps[k], k, l);
             ps[k].part_begin = xb ? k * G : t0;
             ps[k].part_end = xb ? (k + 1) * G : t;
             ps[k].resident = B.res[l][k];
+        }
+    }
+    // persistent engine: segments, warp lists and per-pair scalars over the segment ranges
+    for (int l = 0; l < B.L; ++l) {
+        if (!B.pers[l]) continue;
+        if (B.n == 1)
+            pair_iter((PairIter *)(img.data() + B.pairs_off[l][0]), (PairIter *)(img.data() + B.pairs_off[l][1]), 0, l);
+        memcpy(img.data() + B.pseg_off[l], B.psegs[l].data(), sizeof(PSeg) * B.psegs[l].size());
+        memcpy(img.data() + B.pwoff_off[l], B.pwoff[l].data(), sizeof(int) * B.pwoff[l].size());
+        memcpy(img.data() + B.pwseg_off[l], B.pwseg[l].data(), sizeof(int) * B.pwseg[l].size());
+        PairScalars *ps = (PairScalars *)(img.data() + B.pscal_off[l]);
+        for (int k = 0; k < B.n; ++k) {
+            scalars(ps[k], k, l);
+            ps[k].part_begin = B.pbegin[l][k];
+            ps[k].part_end = B.pend[l][k];
+            ps[k].resident = B.pbegin[l][k] == B.pend[l][k];  // not on this engine: skipped by the reductions
         }
     }
     // work already queued on any stream may still read another layout's tables in this region
@@ -592,9 +771,33 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     launch_admm_resident(r, B.nres[l], B.res_nc[l], B.res_smem[l], prec, pflow, s);
                 }
             }
+            // persistent engine: every inner iteration of the level's other pairs in one launch
+            const bool persl = B.pers[l];
+            char *T = ctx->arena + B.table_off;
+            if (persl && p->iters > 0) {
+                const int N = (int)B.psegs[l].size();
+                cudaMemsetAsync(T + B.pctr_off[l], 0, sizeof(unsigned) * (N + n), s);
+                PersistArgs a{};
+                a.k = k;
+                a.pairs = (const PairIter *)(T + B.pairs_off[l][in32 ? 1 : 0]);
+                a.scal = (const PairScalars *)(T + B.pscal_off[l]);
+                a.segs = (const PSeg *)(T + B.pseg_off[l]);
+                a.woff = (const int *)(T + B.pwoff_off[l]);
+                a.wseg = (const int *)(T + B.pwseg_off[l]);
+                a.nwarps = B.pnwarps[l];
+                a.flags = (unsigned *)(T + B.pctr_off[l]);
+                a.pbar = a.flags + N;
+                a.partials = (double *)(T + B.ppart_off[l]);
+                a.parity = start;
+                a.iters = p->iters;
+                a.check = p->tol > 0.0;
+                a.final_res = last_warp;
+                a.tol = p->tol;
+                launch_admm_persist(a, prec, pflow, s);
+            }
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
             // the non-resident pairs (ALG1)
-            const bool streamed = batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1;
+            const bool streamed = !persl && (batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1);
             for (int it = 0; streamed && it < p->iters; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it == p->iters - 1;
@@ -676,7 +879,13 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 cur = fin;
             }
             if (last_warp && p->iters > 0 && !res1) {
-                if (batched) {
+                if (persl) {
+                    double *pp = (double *)(T + B.ppart_off[l]);
+                    if (batched)
+                        launch_reduce_check_batched(pp, (const PairScalars *)(T + B.pscal_off[l]), n, 0.0, 0, 1, s);
+                    else
+                        launch_sum(pp, (int)B.psegs[l].size(), &pc[0].misc->res_final, s);
+                } else if (batched) {
                     launch_reduce_check_batched(bpart, ps, n, 0.0, 0, 1, s);
                 } else {
                     const Geom g = geom_of(*pc[0].pl, l);
@@ -711,6 +920,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
 // ------------------------------------------------------------ strip-height autotuner
 // Whether level l of layout B runs inner iterations on the streaming ADMM kernel.
 bool streamed_admm(const Batch &B, const of_params *p, int l) {
+    if (B.pers[l]) return false;
     if (p->method != OF_PADMM_I && p->method != OF_PADMM_II) return false;
     if (p->engine == OF_ENGINE_PLAIN || p->iters <= 0 || l < B.out_level || l >= B.L) return false;
     return B.n > 1 ? B.ntiles[l] > 0 : !use_resident(p, geom_of(B.pl[0], l));
@@ -834,13 +1044,14 @@ of_status resolve_rows(of_ctx *ctx, Batch &B, const of_params *p) {
 }
 
 of_status get_graph(of_ctx *ctx, const Batch &B, const of_params *p, cudaGraphExec_t *out, cudaGraph_t *graph_out = nullptr) {
-    // a single-pair solve lays its data out from the arena's start, over any batch's tables
-    if (B.n <= 1) ctx->tables_key.clear();
+    // a solve lays its data out from the arena's start, over any other layout's tables; one
+    // without tables of its own leaves none intact
+    if (B.table_bytes == 0) ctx->tables_key.clear();
     auto it = ctx->graphs.find(B.key);
     if (it != ctx->graphs.end()) {
-        // a cached batch graph reads its tables from the arena: restore them if another batch
-        // layout has replaced them since
-        if (B.n > 1 && ctx->tables_key != B.key) {
+        // a cached graph reads its tables from the arena: restore them if another layout has
+        // replaced them since
+        if (B.table_bytes > 0 && ctx->tables_key != B.key) {
             of_status st = upload_tables(ctx, B, p);
             if (st != OF_OK) return st;
         }
@@ -877,6 +1088,7 @@ of_status read_stats(of_ctx *ctx, const Batch &B, int q, const of_params *p, cud
     stats->residual = p->iters > 0 ? sqrt(m.res_final / rows) : 0.0;
     stats->energy = m.energy;
     stats->dual_value = (p->method == OF_PDR || p->method == OF_CP) ? NAN : m.dual;
+    if (m.timeout) return fail(OF_ETIMEOUT, "a bounded wait of the persistent engine ran out");
     if (!isfinite(stats->residual) || !isfinite(stats->energy))
         return fail(OF_ENUMERIC, "non-finite residual or energy (NaN/Inf in the inputs or parameters?)");
     return OF_OK;
@@ -994,6 +1206,86 @@ of_status of_resident_clusters(int *cluster_ctas, int *max_active) {
     *cluster_ctas = admm_resident_cluster();
     *max_active = admm_resident_max_clusters();
     OF_CUDA(cudaGetLastError());
+    return OF_OK;
+}
+
+of_status of_persistent_selftest(int H, int W, int iters, int withhold, double wait_ms, int *timed_out,
+                                 int *segments) {
+    if (!timed_out || H < 1 || W < 1 || iters < 1 || !(wait_ms > 0.0) || !isfinite(wait_ms))
+        return fail(OF_EINVAL, "of_persistent_selftest: bad arguments");
+    of_params p;
+    of_default_params(&p);
+    p.engine = OF_ENGINE_PERSISTENT;
+    const Coefs k = coefs_of(&p);
+    const int cap = persist_capacity(k, PREC_F32, PREC_F32);
+    if (cap <= 0) return fail(OF_ECUDA, "of_persistent_selftest: no occupancy for the persistent kernel");
+    const Geom g{H, W, pitch_of(W)};
+    PersistPlan pp = plan_persist({g}, cap * admm_fused_warps());
+    const int N = (int)pp.segs.size();
+    if (withhold >= N) return fail(OF_EINVAL, "of_persistent_selftest: withhold beyond the segment count");
+    if (segments) *segments = N;
+    // one device block: 2 x 13 state planes, 3 data planes, the pair's scalars and the tables
+    const size_t plane = align_up((size_t)g.H * g.pitch * 4, 256);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off += align_up(b, 256);
+        return o;
+    };
+    const size_t o_st = take(2 * NFIELDS * plane), o_dat = take(3 * plane), o_misc = take(sizeof(Misc));
+    const size_t o_pi = take(sizeof(PairIter)), o_ps = take(sizeof(PairScalars)), o_seg = take(sizeof(PSeg) * N);
+    const size_t o_woff = take(sizeof(int) * pp.woff.size()), o_wseg = take(sizeof(int) * N);
+    const size_t o_ctr = take(sizeof(unsigned) * (N + 1)), o_part = take(sizeof(double) * N);
+    char *D = nullptr;
+    cudaError_t e = cudaMalloc(&D, off);
+    if (e != cudaSuccess) return fail(OF_ECUDA, std::string("of_persistent_selftest: cudaMalloc: ") + cudaGetErrorString(e));
+    Misc *misc = (Misc *)(D + o_misc);
+    PairIter pi{};
+    pi.g = g;
+    pi.buf[0] = fields_at(D + o_st, plane);
+    pi.buf[1] = fields_at(D + o_st + NFIELDS * plane, plane);
+    pi.Ix = D + o_dat;
+    pi.Iy = D + o_dat + plane;
+    pi.It = D + o_dat + 2 * plane;
+    pi.ms_max = &misc->ms_max;
+    PairScalars ps{};
+    ps.res_check = &misc->res_check;
+    ps.res_final = &misc->res_final;
+    ps.done = &misc->done;
+    ps.iters = &misc->iters;
+    ps.part_begin = 0;
+    ps.part_end = N;
+    ps.rows = 3.0 * H * W;
+    ps.timeout = &misc->timeout;
+    e = cudaMemset(D, 0, off);
+    if (e == cudaSuccess) e = cudaMemcpy(D + o_pi, &pi, sizeof(pi), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D + o_ps, &ps, sizeof(ps), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D + o_seg, pp.segs.data(), sizeof(PSeg) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D + o_woff, pp.woff.data(), sizeof(int) * pp.woff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(D + o_wseg, pp.wseg.data(), sizeof(int) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        PersistArgs a{};
+        a.k = k;
+        a.pairs = (const PairIter *)(D + o_pi);
+        a.scal = (const PairScalars *)(D + o_ps);
+        a.segs = (const PSeg *)(D + o_seg);
+        a.woff = (const int *)(D + o_woff);
+        a.wseg = (const int *)(D + o_wseg);
+        a.nwarps = pp.nwarps;
+        a.flags = (unsigned *)(D + o_ctr);
+        a.pbar = a.flags + N;
+        a.partials = (double *)(D + o_part);
+        a.iters = iters;
+        a.wait_ns = (long long)(wait_ms * 1e6);
+        a.withhold = withhold;
+        e = launch_admm_persist(a, PREC_F32, PREC_F32, nullptr);
+    }
+    int to = 0;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&to, &misc->timeout, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(D);
+    if (e != cudaSuccess) return fail(OF_ECUDA, std::string("of_persistent_selftest: ") + cudaGetErrorString(e));
+    *timed_out = to ? 1 : 0;
     return OF_OK;
 }
 

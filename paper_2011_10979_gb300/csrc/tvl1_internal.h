@@ -57,6 +57,7 @@ struct PairScalars {
     int part_begin, part_end;
     double rows;
     int resident, pad_;  // resident: this pair's level runs on the level-resident engine
+    int *timeout;        // set when a bounded device-side wait of the pair's launch ran out
 };
 
 // One work-list entry of a batched launch: pair index, tile column, tile row.
@@ -118,6 +119,34 @@ struct ResArgs {
     int iters = 0, check = 0, final_res = 0;
     double tol = 0.0;
 };
+// Persistent engine of the ADMM methods (k_admm_persist.cuh): one launch per warp of a level runs
+// every inner iteration.  A segment is strip sx (admm_fused_strip_w() output columns) by row band
+// t of m (rows [t H / m, (t + 1) H / m)) of pair `pair`; a pair's segments are numbered
+// t * S + sx from its first one, S = its strip count, and every band has at least two rows
+// unless m = 1.
+struct __align__(16) PSeg {
+    int pair, sx, t, m;
+};
+struct PersistArgs {
+    Coefs k{};
+    const PairIter *pairs = nullptr;    // per pair: geometry, both state buffers, data, a~, stop flag
+    const PairScalars *scal = nullptr;  // per pair: part_begin/part_end = its segment range
+    const PSeg *segs = nullptr;
+    const int *woff = nullptr, *wseg = nullptr;  // warp w holds segments wseg[woff[w] .. woff[w + 1])
+    int nwarps = 0;
+    unsigned *flags = nullptr;          // per segment: iterations finished in this launch (zeroed before)
+    unsigned *pbar = nullptr;           // per pair: stopping-test arrivals in this launch (zeroed before)
+    double *partials = nullptr;         // per segment: FP64 residual partial
+    int parity = 0, iters = 0, check = 0, final_res = 0;
+    double tol = 0.0;
+    long long wait_ns = 2000000000LL;   // bound of every device-side wait
+    int withhold = -1;                  // self-test: this segment never publishes its counter
+};
+// Co-resident blocks (of admm_fused_warps() warps) of the persistent instance for these storage
+// types and method, over the whole device.
+int persist_capacity(const Coefs &k, int prec, int prec_flow);
+cudaError_t launch_admm_persist(const PersistArgs &a, int prec, int prec_flow, cudaStream_t s);
+
 int admm_resident_cluster();           // CTAs per cluster: 16 where the device schedules it, else 8, else 0 (off)
 int admm_resident_max_clusters();      // such clusters the device runs at once (cudaOccupancyMaxActiveClusters)
 // dynamic shared memory of one CTA for this level in a cluster of nc CTAs (0: the largest cluster)

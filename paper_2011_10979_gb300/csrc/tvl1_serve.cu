@@ -242,6 +242,9 @@ of_status of_server_start(of_ctx *ctx, const of_params *params, size_t hbm_budge
     cudaGetDevice(&dev);
     Server *S = new Server();
     S->params = *params;
+    // slots run on concurrent streams: a persistent launch needs the whole GPU to itself (its
+    // warps wait on each other), so the slots take the per-iteration engines instead
+    if (S->params.engine == OF_ENGINE_PERSISTENT) S->params.engine = OF_ENGINE_FUSED;
     S->device = dev;
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);

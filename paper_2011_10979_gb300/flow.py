@@ -18,10 +18,10 @@ _lib = None
 OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_ETIMEOUT, OF_ENUMERIC, OF_EBUSY = range(7)
 OF_PADMM_I, OF_PADMM_II, OF_PDR, OF_CP = 0, 1, 2, 3
 OF_PREC_FP32, OF_PREC_FP16, OF_PREC_BF16 = 0, 1, 2
-OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT = 0, 1, 2, 3
+OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT, OF_ENGINE_PERSISTENT = 0, 1, 2, 3, 4
 
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
-           "of_solve_kernel_count", "of_rows_per_warp", "of_resident_clusters", "of_solve",
+           "of_solve_kernel_count", "of_rows_per_warp", "of_resident_clusters", "of_persistent_selftest", "of_solve",
            "of_solve_host", "of_solve_batch", "of_pyr_down", "of_upsample", "of_derivatives",
            "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_cp_iterate",
            "of_fields_bytes", "of_energy",
@@ -80,6 +80,7 @@ def lib():
             "of_solve_kernel_count": (ctypes.c_longlong, [vp, i, i, P(of_params)]),
             "of_rows_per_warp": (i, [vp, i, P(i), P(i), P(of_params), P(i)]),
             "of_resident_clusters": (i, [P(i), P(i)]),
+            "of_persistent_selftest": (i, [i, i, i, i, d, P(i), P(i)]),
             "of_solve": (i, [vp, vp, vp, i, i, i, P(of_params), vp, vp, vp, i, vp, P(of_stats)]),
             "of_solve_host": (i, [vp, vp, vp, i, i, P(of_params), vp, vp, vp, vp, P(of_stats)]),
             "of_solve_batch": (i, [vp, i, P(vp), P(vp), P(i), P(i), P(i), P(of_params), P(vp), P(vp), P(vp),
@@ -192,6 +193,13 @@ def of_resident_clusters() -> tuple:
     nc, act = ctypes.c_int(0), ctypes.c_int(0)
     check(lib().of_resident_clusters(ctypes.byref(nc), ctypes.byref(act)))
     return nc.value, act.value
+
+
+def of_persistent_selftest(H, W, iters, withhold, wait_ms) -> tuple:
+    """(timed_out, segments) of the persistent engine's bounded-wait self-test."""
+    to, nseg = ctypes.c_int(0), ctypes.c_int(0)
+    check(lib().of_persistent_selftest(H, W, iters, withhold, float(wait_ms), ctypes.byref(to), ctypes.byref(nseg)))
+    return to.value, nseg.value
 
 
 def of_solve(ctx: Context, I0, I1, params: of_params, want_w=False, stats=True, stream=None):
