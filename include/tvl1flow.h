@@ -186,6 +186,14 @@ of_status of_resident_clusters(int *cluster_ctas, int *max_active);
 of_status of_persistent_selftest(int H, int W, int iters, int withhold, double wait_ms, int *timed_out,
                                  int *segments);
 
+/* Bandwidth of the L2 cache for a working set of `bytes` (half read, half written, FP32 words):
+ * one kernel streams the set `passes` times, loading with the L2-only cache hint, after one warm
+ * launch; *gbps receives (read + written bytes) / time.  It is the roofline denominator of the
+ * pyramid levels whose state stays in L2 between inner iterations (a working set under the
+ * 129 MB L2).  Allocates and frees its buffers; synchronises the device.  OF_EINVAL for
+ * bytes < 4096 or passes < 1, OF_ECUDA when a CUDA call fails. */
+of_status of_l2_bandwidth(size_t bytes, int passes, double *gbps);
+
 /* Solves one pair (whole schedule: pyramid, levels, warps, inner iterations; Sec. 3-4).
  * I0, I1: H x W FP32 images (device, pitch `pitch`).  u, v (and w unless NULL): outputs of size
  * H_l x W_l at level params->out_level, FP32, pitch `out_pitch` (>= W_l).  stats: optional; if

@@ -12,11 +12,14 @@
 // Iterations: iteration k of a segment reads buffer (parity + k) & 1 and writes the other.  It
 // needs, from the previous iteration, the fields within two rows above, one row below, two columns
 // west and one east of its own outputs: those come only from the eight segments around it (row
-// bands of at least two rows).  So instead of a grid-wide barrier each segment publishes a
-// counter of finished iterations (release: fence, then a relaxed store at GPU scope) and, before
-// iteration k, waits until its neighbours' counters reach k (relaxed loads, then an acquire
-// fence).  The same wait covers the write-after-read hazard: a neighbour that finished iteration
-// k - 1 has read everything it needs from the buffer this segment now overwrites.
+// bands of at least two rows).  So instead of a grid-wide barrier each segment has a counter of
+// finished iterations, which its warp publishes after finishing all its segments of an iteration
+// (release: fence, then relaxed stores at GPU scope), and before iteration k each segment waits
+// until its neighbours' counters reach k (relaxed loads, then an acquire fence).  The same wait
+// covers the write-after-read hazard: a neighbour that finished iteration k - 1 has read
+// everything it needs from the buffer this segment now overwrites.  A warp publishes an
+// iteration only when it has finished it for all its segments, so the warp furthest behind only
+// ever waits on counters that are already published: no cycle of waits can form.
 //
 // Stopping test (tolerance > 0, every 10th iteration): each segment stores its FP64 residual
 // partial and arrives at its pair's counter; every warp of the pair waits for all of the pair's
@@ -180,11 +183,16 @@ __global__ void __launch_bounds__(roll::WARPS * 32, PERSIST_MIN_BLOCKS) k_admm_p
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
                 if (lane == 0) A.partials[s] = v;
             }
-            // publish: this warp's stores of the segment, then its finished-iteration counter
-            fence_acq_rel();
-            __syncwarp();
-            if (lane == 0 && s != A.withhold) st_relaxed(A.flags + s, (unsigned)(it + 1));
         }
+        // publish once per iteration: this warp's stores of all its segments, then their
+        // finished-iteration counters (a warp holding many segments pays one fence)
+        fence_acq_rel();
+        __syncwarp();
+        if (lane == 0)
+            for (int q = s_lo; q < s_hi; ++q) {
+                const int s = A.wseg[q];
+                if (s != A.withhold) st_relaxed(A.flags + s, (unsigned)(it + 1));
+            }
         if (checking && !check_pairs(A, s_lo, s_hi, (unsigned)((it + 1) / 10))) return;
     }
 }

@@ -21,7 +21,7 @@ OF_PREC_FP32, OF_PREC_FP16, OF_PREC_BF16 = 0, 1, 2
 OF_ENGINE_FUSED, OF_ENGINE_PLAIN, OF_ENGINE_STREAM, OF_ENGINE_RESIDENT, OF_ENGINE_PERSISTENT = 0, 1, 2, 3, 4
 
 EXPORTS = ("of_default_params", "of_create", "of_destroy", "of_last_error", "of_arena_bytes",
-           "of_solve_kernel_count", "of_rows_per_warp", "of_resident_clusters", "of_persistent_selftest", "of_solve",
+           "of_solve_kernel_count", "of_rows_per_warp", "of_resident_clusters", "of_persistent_selftest", "of_l2_bandwidth", "of_solve",
            "of_solve_host", "of_solve_batch", "of_pyr_down", "of_upsample", "of_derivatives",
            "of_warp_linearise", "of_admm_iterate", "of_admm_iterate_noalloc", "of_pdr_iterate", "of_cp_iterate",
            "of_fields_bytes", "of_energy",
@@ -81,6 +81,7 @@ def lib():
             "of_rows_per_warp": (i, [vp, i, P(i), P(i), P(of_params), P(i)]),
             "of_resident_clusters": (i, [P(i), P(i)]),
             "of_persistent_selftest": (i, [i, i, i, i, d, P(i), P(i)]),
+            "of_l2_bandwidth": (i, [sz, i, P(d)]),
             "of_solve": (i, [vp, vp, vp, i, i, i, P(of_params), vp, vp, vp, i, vp, P(of_stats)]),
             "of_solve_host": (i, [vp, vp, vp, i, i, P(of_params), vp, vp, vp, vp, P(of_stats)]),
             "of_solve_batch": (i, [vp, i, P(vp), P(vp), P(i), P(i), P(i), P(of_params), P(vp), P(vp), P(vp),
@@ -200,6 +201,13 @@ def of_persistent_selftest(H, W, iters, withhold, wait_ms) -> tuple:
     to, nseg = ctypes.c_int(0), ctypes.c_int(0)
     check(lib().of_persistent_selftest(H, W, iters, withhold, float(wait_ms), ctypes.byref(to), ctypes.byref(nseg)))
     return to.value, nseg.value
+
+
+def of_l2_bandwidth(nbytes: int, passes: int) -> float:
+    """GB/s of the L2-only streaming probe over a working set of `nbytes`."""
+    g = ctypes.c_double(0.0)
+    check(lib().of_l2_bandwidth(nbytes, passes, ctypes.byref(g)))
+    return g.value
 
 
 def of_solve(ctx: Context, I0, I1, params: of_params, want_w=False, stats=True, stream=None):
