@@ -186,6 +186,45 @@ def run_batch16(args):
     print(json.dumps({"legs": "batch16", "batch": r}))
 
 
+def run_level(args):
+    """Single-level solves for a profiler: the 40x30 and 640x480 levels of the bench pair's kind
+    (one warp, 30 inner iterations, three solves each) on the given engine, strip height
+    --rows-per-warp (8 unless set).  A 40x30 level runs a handful of warps, each walking its strip
+    alone on its SM, so it shows the latency of one warp's row steps."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2011_10979_gb300 import flow, synth
+    from paper_2011_10979_gb300.build import build
+    build()
+    ctx = flow.Context(0)
+    eng = {"stream": flow.OF_ENGINE_STREAM, "persistent": flow.OF_ENGINE_PERSISTENT, "fused": flow.OF_ENGINE_FUSED}
+    ty = args.rows_per_warp if args.rows_per_warp > 0 else 8
+    for (h, w) in ((30, 40), (480, 640)):
+        pr = synth.affine_rect_pair(h, w) if h >= 120 else synth.random_affine_rect_pair(h, w, 3)
+        I0, I1 = torch.from_numpy(pr.I0).to(dev), torch.from_numpy(pr.I1).to(dev)
+        P = flow.default_params(lam=LAM, beta=BETA, levels=1, warps=1, iters=30, engine=eng[args.engine],
+                                rows_per_warp=ty)
+        for _ in range(3):
+            flow.of_solve(ctx, I0, I1, P, stats=False)
+        torch.cuda.synchronize(dev)
+    ctx.close()
+    print(json.dumps({"legs": "level", "engine": args.engine, "rows_per_warp": ty}))
+
+
+def run_serving(args):
+    """The serving leg alone, at its sustained and its overload rate for 60 s each (one GPU)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2011_10979_gb300 import flow
+    from paper_2011_10979_gb300.build import build
+    build()
+    out = {rate: serving_measure(flow, torch, dev, rate_hz=rate, duration_s=60.0, drain_s=10.0)
+           for rate in (50.0, 200.0)}
+    print(json.dumps({"legs": "serving", "serving_60s": {"%.0f_req_per_s" % k: v for k, v in out.items()}}))
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -263,8 +302,8 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t_plain = e0.elapsed_time(e1) / 3 / 1e3
-        serving = serving_measure(flow, torch, dev)
-        serving50 = serving_measure(flow, torch, dev, rate_hz=50.0)
+        serving = serving_measure(flow, torch, dev, rate_hz=50.0)
+        serving50 = serving_measure(flow, torch, dev, rate_hz=200.0)
         batch = batch_measure(flow, torch, dev, fp32_flow=1)
         batch_all16 = batch_measure(flow, torch, dev, fp32_flow=0)
         batch_fp32 = batch_measure(flow, torch, dev, prec=flow.OF_PREC_FP32)
@@ -301,7 +340,7 @@ def run_ours(args):
             "roofline": roof,
             "batch": batch,
             "serving": serving,
-            "serving_50hz": serving50,
+            "serving_overload_200hz": serving50,
             "batch_all16": batch_all16,
             "batch_fp32": batch_fp32,
             "precision_1024x436": prec_line,
@@ -448,11 +487,19 @@ def solvers_measure(flow, torch, dev, I0, I1, pr):
     return out
 
 
-def serving_measure(flow, torch, dev, rate_hz=20.0, duration_s=10.0, max_active=8):
-    """Serving loop under Poisson arrivals (rate_hz for duration_s), request sizes drawn from
-    {320x240: 40%, 640x480: 30%, 1024x436: 20%, 1920x1080: 8%, 3840x2160: 2%} with layered motion
-    up to 30 px (one seeded pair per size, reused), BF16 duals + FP32 flow, 5x10x100 schedule.
-    Latency = submit to result on the host; p50/p99 over all requests."""
+SERVE_DIST = ("Poisson arrivals, sizes {320x240: 40%, 640x480: 30%, 1024x436: 20%, 1920x1080: 8%, 3840x2160: 2%}, "
+              "layered motion <= 30 px, BF16 duals + FP32 flow, 5 levels x 10 warps x 100 iterations")
+
+
+def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0, max_active=32):
+    """The serving loop under Poisson arrivals (rate_hz for duration_s) of the serving size mix
+    (one seeded layered pair per size, reused).  Every step of the loop advances all admitted
+    requests by one warp, their inner iterations sharing launches.  Throughput counts the requests
+    finished inside the arrival window; after it the loop gets drain_s to finish the rest, and
+    what is still queued or running then is reported as unfinished (past saturation the queue only
+    grows).  Latency = submit to result on the host, p50/p99 over the finished requests.  Beside it,
+    the same request sequence through one of_solve call at a time (the plain single-pair path):
+    the sum of the per-size device times of a solve."""
     from paper_2011_10979_gb300 import synth
     imgs = {}
     for (H, W), _ in synth.SERVE_MIX:
@@ -462,17 +509,30 @@ def serving_measure(flow, torch, dev, rate_hz=20.0, duration_s=10.0, max_active=
     P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
                             precision=flow.OF_PREC_BF16, fp32_last_warp=1, fp32_flow=1)
     ctx = flow.Context(dev.index)
+    # the plain single-pair path: device time of one whole solve per size
+    stream = torch.cuda.current_stream(dev)
+    single_ms = {}
+    for k, pr in imgs.items():
+        I0, I1 = torch.from_numpy(pr.I0).to(dev), torch.from_numpy(pr.I1).to(dev)
+        flow.of_solve(ctx, I0, I1, P, stats=False)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(2):
+            flow.of_solve(ctx, I0, I1, P, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        single_ms[k] = e0.elapsed_time(e1) / 2
     flow.of_server_start(ctx, P, 0, max_active)
     try:
-        # warm-up: one request per size captures each size's CUDA graph
-        warm = [(flow.of_server_submit(ctx, imgs[k].I0, imgs[k].I1), k) for k in imgs]
+        warm = [(flow.of_server_submit(ctx, imgs[k].I0, imgs[k].I1), k) for k in imgs]  # pinned pool, memory pool
         for rid, k in warm:
             while flow.of_server_poll(ctx, rid, k) is None:
                 time.sleep(0.001)
-        pending, lat = {}, []
+        pending, lat, done_at = {}, [], []
         t0 = time.perf_counter()
         nxt = 0
-        while nxt < len(arrivals) or pending:
+        while (nxt < len(arrivals) or pending) and time.perf_counter() - t0 < duration_s + drain_s:
             now = time.perf_counter() - t0
             while nxt < len(arrivals) and arrivals[nxt] <= now:
                 k = sizes[nxt]
@@ -482,20 +542,27 @@ def serving_measure(flow, torch, dev, rate_hz=20.0, duration_s=10.0, max_active=
                 r = flow.of_server_poll(ctx, rid, pending[rid])
                 if r is not None:
                     lat.append(r[2])
+                    done_at.append(time.perf_counter() - t0)
                     del pending[rid]
             time.sleep(0.0005)
-        elapsed = time.perf_counter() - t0
+        unfinished = len(pending) + (len(arrivals) - nxt)
     finally:
         flow.of_server_stop(ctx)
         ctx.close()
     lat = np.array(lat)
-    work = sum(mpix_iter_per_flow(h=h, w=w) for h, w in sizes)
-    return {"workload": "Poisson %.0f req/s for %.0f s, size mix 320x240..3840x2160, layered motion <= 30 px"
-                        % (rate_hz, duration_s),
-            "requests": int(len(lat)), "value": len(lat) / elapsed, "unit": "flows/s",
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "gpix_iter_per_s": work / 1e3 / elapsed, "max_active": max_active,
-            "storage": "bf16_duals+fp32_flow"}
+    in_window = int(np.sum(np.array(done_at) <= duration_s))
+    work = sum(mpix_iter_per_flow(h=h, w=w) for h, w in sizes[:len(lat)])
+    seq_s = sum(single_ms[k] for k in sizes) / 1e3
+    return {"workload": "%s, %.0f req/s for %.0f s" % (SERVE_DIST, rate_hz, duration_s),
+            "offered": len(arrivals), "finished": int(len(lat)), "finished_in_window": in_window,
+            "unfinished_after_drain": int(unfinished), "drain_s": drain_s,
+            "value": in_window / duration_s, "unit": "flows/s",
+            "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+            "gpix_iter_per_s": work / 1e3 / (done_at[-1] if done_at else 1.0), "max_active": max_active,
+            "single_pair_path": {"value": len(sizes) / seq_s, "unit": "flows/s",
+                                 "note": "the same requests through one of_solve at a time (device time)",
+                                 "ms_per_solve": {"%dx%d" % (w, h): round(v, 3) for (h, w), v in single_ms.items()}}}
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streaming pADMM kernel on the
@@ -539,11 +606,16 @@ def kernel_roofline(flow, torch, dev, pr, reps=20):
     per = (t[220] - t[20]) / 200.0
     bytes_per_launch = 92.0 * H * W
     achieved = bytes_per_launch / per / 1e9
+    # the level's working set stays in L2: its bandwidth for a working set of the same size
+    # (half read, half written, streamed 400 times in one launch)
+    l2 = flow.of_l2_bandwidth(int(bytes_per_launch), 400)
     return {"kernel": "k_admm_roll<float,float,1,0,8> (640x480 level)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
             "traffic": ROLL_640_DRAM_BYTES, "us_per_launch": per * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch,
             "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 200",
-            "note": "the 640x480 level's 28 MB state stays in the 129 MB L2 between iterations"}
+            "l2_peak": l2, "frac_of_l2": achieved / l2,
+            "note": "the 640x480 level's 28 MB state stays in the 129 MB L2 between iterations; l2_peak is the "
+                    "library's L2 streaming probe over a 28 MB read+write working set"}
 
 
 def main():
@@ -555,7 +627,9 @@ def main():
     # "solve": only the timed single-pair solve (and its e2e leg), e.g. as a short command to run
     # under a profiler; "batch16": only a 16-pair batch (one GPU), likewise; "all" (default) adds the
     # roofline, plain, batch, serving, precision, solver and CPU-baseline legs
-    ap.add_argument("--legs", default="all", choices=["all", "solve", "batch16"])
+    ap.add_argument("--legs", default="all", choices=["all", "solve", "batch16", "serving", "level"])
+    # the level leg: single-level solves for a profiler (engine and strip height as given)
+    ap.add_argument("--engine", default="stream", choices=["stream", "persistent", "fused"])
     # strip height of the batch16 leg (-1: autotuned; a fixed height makes the launch sequence
     # independent of timing, e.g. under a profiler)
     ap.add_argument("--rows-per-warp", type=int, default=-1, choices=[-1, 0, 1, 2, 8, 32])
@@ -564,6 +638,10 @@ def main():
         run_reference(args)
     elif args.legs == "batch16":
         run_batch16(args)
+    elif args.legs == "serving":
+        run_serving(args)
+    elif args.legs == "level":
+        run_level(args)
     else:
         run_ours(args)
 

@@ -96,8 +96,10 @@ typedef struct {
     int precision;       /* of_precision: storage of the iterated fields; arithmetic is FP32   */
     int fp32_last_warp;  /* 1: the finest level's last warp runs with FP32 storage             */
     int fp32_flow;       /* 1: with 16-bit storage, keep the flow and illumination fields
-                            (w, u, v; pDR also its barred copies) in FP32 and store only the
-                            dual fields and the linearisation data in 16 bits               */
+                            (w, u, v; pDR also its barred copies; ALG1 its barred copies
+                            and its dual y, which moves by constant cp_tau steps) in FP32
+                            and store only the other dual fields and the linearisation
+                            data in 16 bits                                                  */
     int engine;          /* of_engine                                                           */
     int out_level;       /* stop after this pyramid level and return its flow (0 = finest)     */
     float cp_tau;        /* ALG1 dual step (Sec. 4: 0.1)                                        */
@@ -106,19 +108,21 @@ typedef struct {
                             ||M_s|| = max M_s, Prop. 3.1); 1 = the per-pixel diagonal
                             a~_ij = max(M_s(ij), 1e-12), which keeps c(diag(a~) - M_s) positive
                             semidefinite because M_s is diagonal (an extension, not in the paper) */
-    int rows_per_warp;   /* strip height of the fused streaming ADMM kernel (rows each warp
-                            finishes per inner iteration; the strip is 29 columns wide):
+    int rows_per_warp;   /* ADMM methods: strip height of the fused streaming kernel (rows each
+                            warp finishes per inner iteration; the strip is 29 columns wide):
                             0 = chosen per level from the level's size by the built-in rule;
-                            1, 2, 8 or 32 = that height on every streamed level;
+                            1, 2, 8 or 32 = that height on every streamed level.
+                            pDR and ALG1: block height of their per-iteration kernels (blocks
+                            of 32 columns): 0 = 8; 4, 8 or 16 = that height.
                             -1 = autotuned: the first solve of a layout on a context times every
-                            height on each streamed level (a few iterations of the real launch on
-                            the arena, after a device synchronisation) and keeps the fastest for
-                            that context.  The flow does not depend on it (the per-pixel
-                            arithmetic is the same); only the grouping of the residual's
-                            partial sums changes, so the residual (and a stopping decision
-                            taken on it) can differ in the last FP32 digits.  Used by of_solve,
-                            of_solve_batch and the serving loop; the step-level entry points
-                            use the built-in rule.                                              */
+                            height on each level that runs those kernels (a few iterations of the
+                            real launch on the arena, after a device synchronisation) and keeps
+                            the fastest for that context.  The flow does not depend on it (the
+                            per-pixel arithmetic is the same); only the grouping of the
+                            residual's partial sums changes, so the residual (and a stopping
+                            decision taken on it) can differ in the last FP32 digits.  Used by
+                            of_solve and of_solve_batch; the step-level entry points and the
+                            serving loop use the built-in choice.                             */
 } of_params;
 
 typedef struct {
@@ -155,11 +159,11 @@ size_t of_arena_bytes(int H, int W, const of_params *params);
  * error (message in of_last_error). */
 long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *params);
 
-/* Strip heights of the fused streaming ADMM kernel in a solve of n pairs of sizes H[k] x W[k]
- * (n = 1: of_solve; n > 1: of_solve_batch) with these parameters: rows[l] for l in
- * [0, params->levels) is the height used on pyramid level l, 0 where no pair of that level runs on
- * the streaming ADMM kernel (a level-resident launch, pDR, ALG1, the plain engine, or a level below
- * out_level).  With params->rows_per_warp = -1 it runs the autotuner first if this layout is not
+/* Strip heights of the fused streaming ADMM kernel (pDR, ALG1: block heights of their
+ * per-iteration kernels) in a solve of n pairs of sizes H[k] x W[k] (n = 1: of_solve; n > 1:
+ * of_solve_batch) with these parameters: rows[l] for l in [0, params->levels) is the height used on
+ * pyramid level l, 0 where no pair of that level runs on those kernels (a level-resident or
+ * persistent launch, the plain engine, or a level below out_level).  With params->rows_per_warp = -1 it runs the autotuner first if this layout is not
  * tuned on the context yet (allocating the arena and launching kernels; the device is
  * synchronised).  `rows` is caller-owned host memory of params->levels ints.  OF_EINVAL for bad
  * arguments, OF_ENOMEM / OF_ECUDA as for of_solve_batch. */

@@ -12,6 +12,9 @@
 // Batched form: slice z of the grid works on pair k = plist[z] (the level's pairs that are not on
 // the level-resident engine), which reads buf[parity] and writes buf[parity ^ 1]; its partials
 // occupy cp_blocks(args.g) slots from k * cp_blocks(args.g).
+// Storage: the dual y is kept in the flow fields' type TF, like X and Xbar (FP32 under fp32_flow):
+// it moves by constant steps tau = 0.1, which an 8-bit mantissa would round away; only the
+// linearisation data is stored in T.
 #include <math.h>
 
 #include "k_cp_math.cuh"
@@ -21,10 +24,11 @@ namespace tvl1 {
 
 namespace {
 
-constexpr int PX = 32, PY = 8;
+// Blocks of 32 columns by blockDim.y rows: 4, 8 (the default) or 16, the autotuner's choice.
+constexpr int PX = 32, PY_DEFAULT = 8, PY_MAX = 16;
 
 template <typename T, typename TF, bool HAS_W>
-__global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
+__global__ void __launch_bounds__(PX *PY_MAX) k_cp(IterArgs A) {
     __shared__ double red[32];
     int H, W, P;
     Fields in, out;
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
     }
     if (donep && *donep) return;  // uniform per block: the pair's warp met its stopping test
     const float tau = A.k.cp_tau, sg = A.k.cp_sigma, beta = A.k.beta, lam = A.k.lambda;
-    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
     float res = 0.f;
     if (i < H && j < W) {
         // y^{k+1} at pixel (a, b): the projected dual ascent step from grad Xbar^k
@@ -67,12 +71,12 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
             auto gx = [&](int f) { return hx ? ldT<TF>(in.f[f], o + 1) - ldT<TF>(in.f[f], o) : 0.f; };
             auto gy = [&](int f) { return hy ? ldT<TF>(in.f[f], o + P) - ldT<TF>(in.f[f], o) : 0.f; };
             float y0[6], g[6];
-            y0[0] = HAS_W ? ldT<T>(in.f[F_P1], o) : 0.f;
-            y0[1] = HAS_W ? ldT<T>(in.f[F_P2], o) : 0.f;
-            y0[2] = ldT<T>(in.f[F_Q11], o);
-            y0[3] = ldT<T>(in.f[F_Q12], o);
-            y0[4] = ldT<T>(in.f[F_Q21], o);
-            y0[5] = ldT<T>(in.f[F_Q22], o);
+            y0[0] = HAS_W ? ldT<TF>(in.f[F_P1], o) : 0.f;
+            y0[1] = HAS_W ? ldT<TF>(in.f[F_P2], o) : 0.f;
+            y0[2] = ldT<TF>(in.f[F_Q11], o);
+            y0[3] = ldT<TF>(in.f[F_Q12], o);
+            y0[4] = ldT<TF>(in.f[F_Q21], o);
+            y0[5] = ldT<TF>(in.f[F_Q22], o);
             g[0] = HAS_W ? gx(F_WB) : 0.f;
             g[1] = HAS_W ? gy(F_WB) : 0.f;
             g[2] = gx(F_UB);
@@ -94,15 +98,15 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
         const float d3[3] = {HAS_W ? dv(0, 1) : 0.f, dv(2, 3), dv(4, 5)};
         res = cp_primal<HAS_W>(x, d3, ldT<T>(Ixp, o), ldT<T>(Iyp, o), ldT<T>(Itp, o), beta, lam, sg);
         if (HAS_W) {
-            stT<T>(out.f[F_P1], o, y0[0]);
-            stT<T>(out.f[F_P2], o, y0[1]);
+            stT<TF>(out.f[F_P1], o, y0[0]);
+            stT<TF>(out.f[F_P2], o, y0[1]);
             stT<TF>(out.f[F_W], o, x[0]);
             stT<TF>(out.f[F_WB], o, 2.f * x[0] - xold[0]);
         }
-        stT<T>(out.f[F_Q11], o, y0[2]);
-        stT<T>(out.f[F_Q12], o, y0[3]);
-        stT<T>(out.f[F_Q21], o, y0[4]);
-        stT<T>(out.f[F_Q22], o, y0[5]);
+        stT<TF>(out.f[F_Q11], o, y0[2]);
+        stT<TF>(out.f[F_Q12], o, y0[3]);
+        stT<TF>(out.f[F_Q21], o, y0[4]);
+        stT<TF>(out.f[F_Q22], o, y0[5]);
         stT<TF>(out.f[F_U], o, x[1]);
         stT<TF>(out.f[F_V], o, x[2]);
         stT<TF>(out.f[F_UB], o, 2.f * x[1] - xold[1]);
@@ -115,15 +119,21 @@ __global__ void __launch_bounds__(PX *PY) k_cp(IterArgs A) {
     }
 }
 
+int block_rows(int tile_h) { return (tile_h == 4 || tile_h == 16) ? tile_h : PY_DEFAULT; }
+
 template <typename T, typename TF> void launch_t(const IterArgs &a, cudaStream_t s) {
-    dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + PY - 1) / PY, a.pairs ? a.ntiles : 1), blk(PX, PY);
+    const int py = block_rows(a.tile_h);
+    dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + py - 1) / py, a.pairs ? a.ntiles : 1), blk(PX, py);
     if (a.k.beta != 0.f) k_cp<T, TF, true><<<grid, blk, 0, s>>>(a);
     else k_cp<T, TF, false><<<grid, blk, 0, s>>>(a);
 }
 
 }  // namespace
 
-int cp_blocks(Geom g) { return ((g.W + PX - 1) / PX) * ((g.H + PY - 1) / PY); }
+int cp_blocks(Geom g, int tile_h) {
+    const int py = block_rows(tile_h);
+    return ((g.W + PX - 1) / PX) * ((g.H + py - 1) / py);
+}
 
 void launch_cp(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
     if (prec == PREC_F32) launch_t<float, float>(a, s);

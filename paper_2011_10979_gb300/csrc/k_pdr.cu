@@ -18,7 +18,10 @@ namespace tvl1 {
 
 namespace {
 
-constexpr int PX = 32, PY = 8;
+// Blocks of 32 columns by blockDim.y rows: 4, 8 (the default) or 16, the autotuner's choice.
+constexpr int PX = 32, PY_DEFAULT = 8;
+
+int block_rows(int tile_h) { return (tile_h == 4 || tile_h == 16) ? tile_h : PY_DEFAULT; }
 
 // The planes one block works on: the single pair of the launch, or in a batch the pair
 // plist[blockIdx.z] (the level's pairs not on the level-resident engine; all pairs if plist is
@@ -78,7 +81,7 @@ __device__ __forceinline__ size_t partial_slot(const PView &V) {
 template <typename T, typename TF, bool HAS_W>
 __global__ void k_pdr_b(IterArgs A) {
     const PView V = view_of(A);
-    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (i >= H || j >= W) return;
     if (V.done && *V.done) return;
@@ -118,7 +121,7 @@ __device__ __forceinline__ float gs_value(const PView &V, const float *tmp, size
 template <typename T, typename TF, bool HAS_W>
 __global__ void k_pdr_b_red(IterArgs A) {
     const PView V = view_of(A);
-    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (i >= H || j >= W) return;
     if (V.done && *V.done) return;
@@ -147,7 +150,7 @@ template <typename T, typename TF, bool HAS_W>
 __global__ void k_pdr_red_finish(IterArgs A) {
     __shared__ double red[32];
     const PView V = view_of(A);
-    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (V.done && *V.done) return;
     const float *tmp = V.tmp;
@@ -207,7 +210,7 @@ __global__ void k_pdr_red_finish(IterArgs A) {
 template <typename T, typename TF, bool HAS_W>
 __global__ void k_gs_half(IterArgs A, int colour) {
     const PView V = view_of(A);
-    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (i >= H || j >= W || ((i + j) & 1) != colour) return;
     if (V.done && *V.done) return;
@@ -233,7 +236,7 @@ template <typename T, typename TF, bool HAS_W>
 __global__ void k_pdr_finish(IterArgs A) {
     __shared__ double red[32];
     const PView V = view_of(A);
-    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * PY + threadIdx.y;
+    const int j = blockIdx.x * PX + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
     const int H = V.g.H, W = V.g.W, P = V.g.pitch;
     if (V.done && *V.done) return;
     const float *tmp = V.tmp;
@@ -279,7 +282,8 @@ __global__ void k_pdr_finish(IterArgs A) {
 }
 
 template <typename T, typename TF, bool HAS_W> void launch_pdr_w(const IterArgs &a, bool literal, cudaStream_t s) {
-    dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + PY - 1) / PY, a.pairs ? a.ntiles : 1), blk(PX, PY);
+    const int py = literal ? PY_DEFAULT : block_rows(a.tile_h);
+    dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + py - 1) / py, a.pairs ? a.ntiles : 1), blk(PX, py);
     if (literal) {
         k_pdr_b<T, TF, HAS_W><<<grid, blk, 0, s>>>(a);
         for (int sw = 0; sw < a.k.gs_sweeps; ++sw) {
@@ -310,7 +314,10 @@ template <typename T, typename TF> void launch_pdr_t(const IterArgs &a, bool lit
 
 }  // namespace
 
-int pdr_plain_blocks(Geom g) { return ((g.W + PX - 1) / PX) * ((g.H + PY - 1) / PY); }
+int pdr_plain_blocks(Geom g, int tile_h) {
+    const int py = block_rows(tile_h);
+    return ((g.W + PX - 1) / PX) * ((g.H + py - 1) / py);
+}
 int pdr_fused_blocks(Geom g) { return pdr_plain_blocks(g); }
 
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s) { launch_pdr_t<float, float>(a, true, s); }

@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
 // south neighbours of Xbar; the last band row of p2, q12, q22 goes to the south CTA's north ghost
 // row).  Phase B: X' = prox(X + sigma div y') (west and north neighbours of y'), Xbar' = 2X' - X,
 // |X' - X|^2 (the first band row of Xbar' goes to the north CTA's south ghost row).  The state is
-// rounded to the storage type where the one-kernel-per-iteration engine's stores round it.
+// rounded to the storage type where the one-kernel-per-iteration engine's stores round it; y, X
+// and Xbar are all kept in the flow fields' type TF (k_cp.cu).
 enum { C_P1, C_P2, C_Q11, C_Q12, C_Q21, C_Q22, C_W, C_U, C_V, C_WB, C_UB, C_VB, C_IX, C_IY, C_IT };
 __constant__ int kFieldCP[12] = {F_P1, F_P2, F_Q11, F_Q12, F_Q21, F_Q22, F_W, F_U, F_V, F_WB, F_UB, F_VB};
 
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(RT, 1) k_cp_resident(ResArgs A) {
     for_band(npx, W, di, dj, [&](int x, int li, int j) {
         const size_t o = (size_t)(r0 + li) * P + j;
 #pragma unroll
-        for (int k = C_P1; k <= C_Q22; ++k) S[k * PL + x] = (HAS_W || k >= C_Q11) ? ldT<T>(in[k], o) : 0.f;
+        for (int k = C_P1; k <= C_Q22; ++k) S[k * PL + x] = (HAS_W || k >= C_Q11) ? ldT<TF>(in[k], o) : 0.f;
 #pragma unroll
         for (int k = C_W; k <= C_VB; ++k) {
             const float v = (HAS_W || (k != C_W && k != C_WB)) ? ldT<TF>(in[k], o) : 0.f;
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(RT, 1) k_cp_resident(ResArgs A) {
             auto gy = [&](int k) { return hy ? S[k * PL + x + W] - S[k * PL + x] : 0.f; };
             float y[6], g[6], yn[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) y[k] = (HAS_W || k >= 2) ? storage_round<T>(S[k * PL + x]) : 0.f;
+            for (int k = 0; k < 6; ++k) y[k] = (HAS_W || k >= 2) ? storage_round<TF>(S[k * PL + x]) : 0.f;
             g[0] = HAS_W ? gx(C_WB) : 0.f;
             g[1] = HAS_W ? gy(C_WB) : 0.f;
             g[2] = gx(C_UB);
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(RT, 1) k_cp_resident(ResArgs A) {
         const size_t o = (size_t)(r0 + li) * P + j;
 #pragma unroll
         for (int k = C_P1; k <= C_Q22; ++k)
-            if (HAS_W || k >= C_Q11) stT<T>(out[k], o, S[k * PL + x]);
+            if (HAS_W || k >= C_Q11) stT<TF>(out[k], o, S[k * PL + x]);
 #pragma unroll
         for (int k = C_W; k <= C_VB; ++k)
             if (HAS_W || (k != C_W && k != C_WB)) stT<TF>(out[k], o, S[k * PL + x]);

@@ -14,97 +14,9 @@
 
 #include "../../include/tvl1flow.h"
 #include "tvl1_internal.h"
+#include "tvl1_plan.h"
 
-using namespace tvl1;
-
-namespace {
-
-thread_local std::string g_err = "no error";
-
-of_status fail(of_status st, const std::string &msg) {
-    g_err = msg;
-    return st;
-}
-
-#define OF_CUDA(call)                                                                                   \
-    do {                                                                                                \
-        cudaError_t e_ = (call);                                                                        \
-        if (e_ != cudaSuccess)                                                                          \
-            return fail(OF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                   \
-    } while (0)
-
-constexpr int MAX_LEVELS = 16;
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-int level_size(int n, float eta) {
-    int m = (int)floor((double)n * (double)eta + 0.5);
-    return m < 1 ? 1 : m;
-}
-
-// Row pitch in elements: a multiple of 64 elements (>= 128 bytes for every storage type).
-int pitch_of(int W) { return (int)align_up((size_t)W, 64); }
-
-struct Plan {
-    int L = 0, out_level = 0, prec = PREC_F32, pflow = PREC_F32;  // storage of duals/data, of w u v
-    bool use32_last = false;
-    int H[MAX_LEVELS], W[MAX_LEVELS], P[MAX_LEVELS];
-    size_t plane32 = 0, planeT = 0;  // bytes of one finest-size plane in FP32 / storage precision
-    size_t planeS = 0;               // stride of the state planes (fits both storage types)
-    size_t img0[MAX_LEVELS], img1[MAX_LEVELS];
-    size_t I1x, I1y, blur, stA, stB, stA32, stB32, data, data32, tmp, partials, misc, out;
-    int max_blocks = 0;
-    size_t total = 0;
-};
-
-// Device scalars at plan.misc.
-struct Misc {
-    float ms_max;
-    int done;
-    long long iters;
-    double res_check, res_final, energy, dual;
-    int timeout;  // a bounded wait of the persistent engine ran out
-};
-
-of_status validate(const of_params *p, int H, int W) {
-    if (!p) return fail(OF_EINVAL, "params is NULL");
-    if (H < 1 || W < 1) return fail(OF_EINVAL, "image sizes must be >= 1");
-    if (p->method < 0 || p->method > 3) return fail(OF_EINVAL, "unknown method");
-    if (!(p->lambda > 0.f) || !isfinite(p->lambda)) return fail(OF_EINVAL, "lambda must be > 0");
-    if (!(p->beta >= 0.f) || !isfinite(p->beta)) return fail(OF_EINVAL, "beta must be >= 0");
-    if (p->method == OF_CP) {
-        if (!(p->cp_tau > 0.f) || !(p->cp_sigma > 0.f) || !isfinite(p->cp_tau) || !isfinite(p->cp_sigma))
-            return fail(OF_EINVAL, "cp_tau and cp_sigma must be > 0");
-        if (p->engine == OF_ENGINE_PLAIN) return fail(OF_EINVAL, "ALG1 has one (fused) engine");
-    } else if (p->method != OF_PDR) {
-        if (!(p->c > 0.f) || !isfinite(p->c)) return fail(OF_EINVAL, "c must be > 0");
-        if (!(p->a > 0.f) || !isfinite(p->a)) return fail(OF_EINVAL, "a must be > 0");
-        if (!isfinite(p->a_tilde)) return fail(OF_EINVAL, "a_tilde must be finite");
-        if (p->method == OF_PADMM_I && !(p->r > 0.f && p->r < 1.6181f))
-            return fail(OF_EINVAL, "r must lie in (0, (1+sqrt 5)/2)");
-        if (p->method == OF_PADMM_II && !(p->rho > 0.f && p->rho < 2.f)) return fail(OF_EINVAL, "rho must lie in (0, 2)");
-    } else {
-        if (!(p->sigma > 0.f) || !(p->tau > 0.f) || !isfinite(p->sigma) || !isfinite(p->tau))
-            return fail(OF_EINVAL, "sigma and tau must be > 0");
-        if (p->gs_sweeps < 1 || p->gs_sweeps > 64) return fail(OF_EINVAL, "gs_sweeps must lie in [1, 64]");
-    }
-    if (!(p->eta > 0.f && p->eta < 1.f)) return fail(OF_EINVAL, "eta must lie in (0, 1)");
-    if (gauss_taps(p->eta).R < 0) return fail(OF_EINVAL, "eta too small for the pre-smoothing kernel");
-    if (p->levels < 1 || p->levels > MAX_LEVELS) return fail(OF_EINVAL, "levels must lie in [1, 16]");
-    if (p->warps < 1) return fail(OF_EINVAL, "warps must be >= 1");
-    if (p->iters < 0) return fail(OF_EINVAL, "iters must be >= 0");
-    if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(OF_EINVAL, "tol must be >= 0");
-    if (p->precision < 0 || p->precision > 2) return fail(OF_EINVAL, "unknown precision");
-    if (p->engine < 0 || p->engine > 4) return fail(OF_EINVAL, "unknown engine");
-    if (p->a_tilde_mode < 0 || p->a_tilde_mode > 1) return fail(OF_EINVAL, "a_tilde_mode must be 0 or 1");
-    if (p->rows_per_warp != -1 && p->rows_per_warp != 0 && p->rows_per_warp != 1 && p->rows_per_warp != 2 &&
-        p->rows_per_warp != 8 && p->rows_per_warp != 32)
-        return fail(OF_EINVAL, "rows_per_warp must be -1 (autotune), 0 (built-in rule), 1, 2, 8 or 32");
-    if (p->engine == OF_ENGINE_PLAIN && p->precision != OF_PREC_FP32)
-        return fail(OF_EINVAL, "the plain engine runs in FP32 only");
-    if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
-    return OF_OK;
-}
+namespace tvl1 {
 
 Plan make_plan(int H, int W, const of_params *p) {
     Plan pl;
@@ -156,7 +68,7 @@ Plan make_plan(int H, int W, const of_params *p) {
     for (int l = 0; l < pl.L; ++l) {
         const Geom g{pl.H[l], pl.W[l], pl.P[l]};
         mb = std::max({mb, admm_fused_blocks(g, p->rows_per_warp != 0 ? 1 : 0), admm_plain_blocks(g),
-                       pdr_plain_blocks(g), cp_blocks(g), energy_blocks(g)});
+                       pdr_plain_blocks(g, PARTIAL_ROWS_MIN), cp_blocks(g, PARTIAL_ROWS_MIN), energy_blocks(g)});
     }
     pl.max_blocks = mb;
     pl.partials = take(3 * (size_t)mb * sizeof(double));
@@ -165,6 +77,97 @@ Plan make_plan(int H, int W, const of_params *p) {
     pl.out = take(3 * nout * 4);
     pl.total = off;
     return pl;
+}
+
+Coefs coefs_of(const of_params *p) {
+    Coefs k;
+    k.lambda = p->lambda;
+    k.beta = p->beta;
+    k.c = p->c;
+    k.a = p->a;
+    k.r = p->method == OF_PADMM_I ? p->r : 1.f;
+    k.rho = p->rho;
+    k.sigma = p->sigma;
+    k.tau = p->tau;
+    k.a_tilde_fixed = p->a_tilde;
+    k.cp_tau = p->cp_tau;
+    k.cp_sigma = p->cp_sigma;
+    k.a_tilde_mode = p->a_tilde_mode;
+    k.method = p->method;
+    k.gs_sweeps = p->gs_sweeps;
+    return k;
+}
+
+Fields fields_at(char *base, size_t plane) {
+    Fields f;
+    for (int k = 0; k < NFIELDS; ++k) f.f[k] = base + (size_t)k * plane;
+    return f;
+}
+
+}  // namespace tvl1
+
+using namespace tvl1;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+of_status fail(of_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define OF_CUDA(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return fail(OF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    } while (0)
+
+of_status validate(const of_params *p, int H, int W) {
+    if (!p) return fail(OF_EINVAL, "params is NULL");
+    if (H < 1 || W < 1) return fail(OF_EINVAL, "image sizes must be >= 1");
+    if (p->method < 0 || p->method > 3) return fail(OF_EINVAL, "unknown method");
+    if (!(p->lambda > 0.f) || !isfinite(p->lambda)) return fail(OF_EINVAL, "lambda must be > 0");
+    if (!(p->beta >= 0.f) || !isfinite(p->beta)) return fail(OF_EINVAL, "beta must be >= 0");
+    if (p->method == OF_CP) {
+        if (!(p->cp_tau > 0.f) || !(p->cp_sigma > 0.f) || !isfinite(p->cp_tau) || !isfinite(p->cp_sigma))
+            return fail(OF_EINVAL, "cp_tau and cp_sigma must be > 0");
+        if (p->engine == OF_ENGINE_PLAIN) return fail(OF_EINVAL, "ALG1 has one (fused) engine");
+    } else if (p->method != OF_PDR) {
+        if (!(p->c > 0.f) || !isfinite(p->c)) return fail(OF_EINVAL, "c must be > 0");
+        if (!(p->a > 0.f) || !isfinite(p->a)) return fail(OF_EINVAL, "a must be > 0");
+        if (!isfinite(p->a_tilde)) return fail(OF_EINVAL, "a_tilde must be finite");
+        if (p->method == OF_PADMM_I && !(p->r > 0.f && p->r < 1.6181f))
+            return fail(OF_EINVAL, "r must lie in (0, (1+sqrt 5)/2)");
+        if (p->method == OF_PADMM_II && !(p->rho > 0.f && p->rho < 2.f)) return fail(OF_EINVAL, "rho must lie in (0, 2)");
+    } else {
+        if (!(p->sigma > 0.f) || !(p->tau > 0.f) || !isfinite(p->sigma) || !isfinite(p->tau))
+            return fail(OF_EINVAL, "sigma and tau must be > 0");
+        if (p->gs_sweeps < 1 || p->gs_sweeps > 64) return fail(OF_EINVAL, "gs_sweeps must lie in [1, 64]");
+    }
+    if (!(p->eta > 0.f && p->eta < 1.f)) return fail(OF_EINVAL, "eta must lie in (0, 1)");
+    if (gauss_taps(p->eta).R < 0) return fail(OF_EINVAL, "eta too small for the pre-smoothing kernel");
+    if (p->levels < 1 || p->levels > MAX_LEVELS) return fail(OF_EINVAL, "levels must lie in [1, 16]");
+    if (p->warps < 1) return fail(OF_EINVAL, "warps must be >= 1");
+    if (p->iters < 0) return fail(OF_EINVAL, "iters must be >= 0");
+    if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(OF_EINVAL, "tol must be >= 0");
+    if (p->precision < 0 || p->precision > 2) return fail(OF_EINVAL, "unknown precision");
+    if (p->engine < 0 || p->engine > 4) return fail(OF_EINVAL, "unknown engine");
+    if (p->a_tilde_mode < 0 || p->a_tilde_mode > 1) return fail(OF_EINVAL, "a_tilde_mode must be 0 or 1");
+    if (p->method == OF_PDR || p->method == OF_CP) {
+        if (p->rows_per_warp != -1 && p->rows_per_warp != 0 && p->rows_per_warp != 4 && p->rows_per_warp != 8 &&
+            p->rows_per_warp != 16)
+            return fail(OF_EINVAL, "rows_per_warp of pDR and ALG1 (their block height) must be -1 (autotune), 0, 4, 8 "
+                                   "or 16");
+    } else if (p->rows_per_warp != -1 && p->rows_per_warp != 0 && p->rows_per_warp != 1 && p->rows_per_warp != 2 &&
+               p->rows_per_warp != 8 && p->rows_per_warp != 32) {
+        return fail(OF_EINVAL, "rows_per_warp must be -1 (autotune), 0 (built-in rule), 1, 2, 8 or 32");
+    }
+    if (p->engine == OF_ENGINE_PLAIN && p->precision != OF_PREC_FP32)
+        return fail(OF_EINVAL, "the plain engine runs in FP32 only");
+    if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
+    return OF_OK;
 }
 
 struct GraphEntry {
@@ -219,30 +222,7 @@ of_status ensure_arena(of_ctx *ctx, size_t bytes) {
     return OF_OK;
 }
 
-Coefs coefs_of(const of_params *p) {
-    Coefs k;
-    k.lambda = p->lambda;
-    k.beta = p->beta;
-    k.c = p->c;
-    k.a = p->a;
-    k.r = p->method == OF_PADMM_I ? p->r : 1.f;
-    k.rho = p->rho;
-    k.sigma = p->sigma;
-    k.tau = p->tau;
-    k.a_tilde_fixed = p->a_tilde;
-    k.cp_tau = p->cp_tau;
-    k.cp_sigma = p->cp_sigma;
-    k.a_tilde_mode = p->a_tilde_mode;
-    k.method = p->method;
-    k.gs_sweeps = p->gs_sweeps;
-    return k;
-}
 
-Fields fields_at(char *base, size_t plane) {
-    Fields f;
-    for (int k = 0; k < NFIELDS; ++k) f.f[k] = base + (size_t)k * plane;
-    return f;
-}
 
 // Enqueues the whole schedule of one pair on `s` (arena pointers only: graph-capturable).
 // A batch of n pairs solved with one set of parameters.  Pair k owns the arena region
@@ -278,7 +258,6 @@ struct Batch {
     std::string key;
 };
 
-Geom geom_of(const Plan &pl, int l) { return Geom{pl.H[l], pl.W[l], pl.P[l]}; }
 
 // Whether a level of geometry g runs its inner iterations on the level-resident engine: the level
 // fits one cluster's shared memory and, with the default engine, is small enough for the resident
@@ -299,6 +278,13 @@ int batch_tiles(const Batch &B, int l, int ty) {
         nt += ((g.W + SWD - 1) / SWD) * ((g.H + rows - 1) / rows);
     }
     return nt;
+}
+
+// The block height of the pDR and ALG1 per-iteration kernels before any tuning: the parameters'
+// height (4, 8 or 16), else 8; 0 for the ADMM methods, whose levels take a strip height instead.
+int block_height_of(const of_params *p) {
+    if (p->method != OF_PDR && p->method != OF_CP) return 0;
+    return (p->rows_per_warp == 4 || p->rows_per_warp == 16) ? p->rows_per_warp : 8;
 }
 
 // Segments of one level for the persistent engine.  gs: per pair its level geometry, H = 0 for a
@@ -448,8 +434,9 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
                     B.res_smem[l] = std::max(B.res_smem[l], admm_resident_smem(geom_of(B.pl[k], l), p->method, B.res_nc[l]));
             gm.pitch = pitch_of(gm.W);
             B.gmax[l] = gm;
-            B.tile_h[l] = p->rows_per_warp > 0 ? p->rows_per_warp
-                                               : admm_fused_rows_per_warp(strip_rows, p->precision != OF_PREC_FP32);
+            B.tile_h[l] = block_height_of(p) ? block_height_of(p)
+                          : p->rows_per_warp > 0 ? p->rows_per_warp
+                                                 : admm_fused_rows_per_warp(strip_rows, p->precision != OF_PREC_FP32);
             B.ntiles[l] = batch_tiles(B, l, B.tile_h[l]);
             // room for the longest work-list (height 1) when the autotuner will try every height
             const bool admm = p->method == OF_PADMM_I || p->method == OF_PADMM_II;
@@ -466,14 +453,16 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             t += align_up(sizeof(int) * n, 256);
             B.streamlist_off[l] = t;
             t += align_up(sizeof(int) * n, 256);
-            const size_t np = std::max({(size_t)nt, (size_t)n * pdr_plain_blocks(gm), (size_t)n * cp_blocks(gm)});
+            const size_t np = std::max({(size_t)nt, (size_t)n * pdr_plain_blocks(gm, PARTIAL_ROWS_MIN),
+                                        (size_t)n * cp_blocks(gm, PARTIAL_ROWS_MIN)});
             maxpart = std::max(maxpart, np);
         }
         B.table_bytes = t;
         B.partials = maxpart;  // slots for now; an offset once the tables are laid out
     } else {
         for (int l = 0; l < B.L; ++l)
-            B.tile_h[l] = p->rows_per_warp > 0    ? p->rows_per_warp
+            B.tile_h[l] = block_height_of(p)      ? block_height_of(p)
+                          : p->rows_per_warp > 0  ? p->rows_per_warp
                           : p->rows_per_warp == 0 ? admm_fused_tile_h(geom_of(B.pl[0], l), p->precision != OF_PREC_FP32)
                                                   : 0;  // set by the autotuner
     }
@@ -581,7 +570,7 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
         int *rl = (int *)(img.data() + B.reslist_off[l]);
         int *sl = (int *)(img.data() + B.streamlist_off[l]);
         int t = 0, r = 0, ns = 0;
-        const int G = cp ? cp_blocks(B.gmax[l]) : pdr_plain_blocks(B.gmax[l]);
+        const int G = cp ? cp_blocks(B.gmax[l], B.tile_h[l]) : pdr_plain_blocks(B.gmax[l], B.tile_h[l]);
         for (int k = 0; k < B.n; ++k) {
             const Geom g = geom_of(B.pl[k], l);
             pair_iter(pi0, pi1, k, l);
@@ -633,7 +622,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
     const bool pingpong = !pdr && !plain;  // ADMM fused engines and ALG1 read one buffer, write the other
     const GaussTaps taps = gauss_taps(p->eta);
     auto blocks_of = [&](Geom g, int l) {
-        return pdr ? pdr_plain_blocks(g) : cp ? cp_blocks(g) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g, B.tile_h[l]));
+        return pdr ? pdr_plain_blocks(g, plain ? 0 : B.tile_h[l])
+                   : cp ? cp_blocks(g, B.tile_h[l]) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g, B.tile_h[l]));
     };
     const Coefs k = coefs_of(p);
     const int L = B.L;
@@ -693,7 +683,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 launch_upsample(bf[cur].f[F_V], gc, bf[nxt].f[F_V], g, (float)g.H / (float)gc.H, pflow, s);
             }
             const int now = l == L - 1 ? cur : cur ^ 1;
-            launch_fill(bf[now].f + F_P1, prec, F_S - F_P1 + 1, g, 0.f, s);   // duals p, q, s restart at 0
+            // duals p, q, s restart at 0 (ALG1 keeps its dual in the flow fields' type)
+            launch_fill(bf[now].f + F_P1, cp ? pflow : prec, F_S - F_P1 + 1, g, 0.f, s);
             if (!has_w) launch_fill(bf[now].f + F_W, pflow, 1, g, 0.f, s);
             if (pdr || cp) {  // pDR: Xbar = X; ALG1: the extrapolated point starts at X
                 const void *src[3] = {bf[now].f[F_W], bf[now].f[F_U], bf[now].f[F_V]};
@@ -713,7 +704,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 if (switch32) {
                     // precision policy: the finest level's last warp runs with FP32 storage
                     launch_convert(c.buf[cur].f + F_W, pflow, c.buf32[0].f + F_W, PREC_F32, 3, g, s);
-                    launch_convert(c.buf[cur].f + F_P1, prec, c.buf32[0].f + F_P1, PREC_F32, F_S - F_P1 + 1, g, s);
+                    launch_convert(c.buf[cur].f + F_P1, cp ? pflow : prec, c.buf32[0].f + F_P1, PREC_F32,
+                                   F_S - F_P1 + 1, g, s);
                     launch_convert(c.buf[cur].f + F_WB, pflow, c.buf32[0].f + F_WB, PREC_F32, 3, g, s);
                 }
                 const Fields *bf = switch32 ? c.buf32 : bufs_of(c);
@@ -842,12 +834,14 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         a.ntiles = n - B.nres[l];
                         a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
                         a.parity = start;
+                        a.tile_h = B.tile_h[l];
                         launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
                         a.g = B.gmax[l];
                         a.ntiles = n - B.nres[l];
                         a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
                         a.parity = (start + it) & 1;
+                        a.tile_h = B.tile_h[l];
                         launch_cp(a, prec, pflow, s);
                     } else {
                         a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
@@ -874,8 +868,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 if (p->tol > 0.0 && (p->iters & 1))
                     for (int q = 0; q < n; ++q)
                         if (!(res1 || (batched && B.res[l][q])))  // the resident engine writes buf[fin] itself
-                            launch_parity_fix(bufs_of(pc[q])[start], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l), prec,
-                                          pflow, &pc[q].misc->done, 1, s);
+                            launch_parity_fix(bufs_of(pc[q])[start], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l),
+                                              cp ? pflow : prec, pflow, &pc[q].misc->done, 1, s);
                 cur = fin;
             }
             if (last_warp && p->iters > 0 && !res1) {
@@ -917,16 +911,19 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
     }
 }
 
-// ------------------------------------------------------------ strip-height autotuner
-// Whether level l of layout B runs inner iterations on the streaming ADMM kernel.
-bool streamed_admm(const Batch &B, const of_params *p, int l) {
-    if (B.pers[l]) return false;
-    if (p->method != OF_PADMM_I && p->method != OF_PADMM_II) return false;
-    if (p->engine == OF_ENGINE_PLAIN || p->iters <= 0 || l < B.out_level || l >= B.L) return false;
-    return B.n > 1 ? B.ntiles[l] > 0 : !use_resident(p, geom_of(B.pl[0], l));
+// ------------------------------------------------------------ autotuner
+// Whether level l of layout B runs its inner iterations on a per-iteration kernel with a tunable
+// shape: the streaming ADMM kernel (its strip height) or the pDR / ALG1 kernels (their block
+// height), for the pairs the level-resident engine does not take.
+bool tunable_level(const Batch &B, const of_params *p, int l) {
+    if (l < B.out_level || l >= B.L || B.pers[l]) return false;
+    if (p->engine == OF_ENGINE_PLAIN || p->iters <= 0) return false;
+    if (p->method == OF_PADMM_I || p->method == OF_PADMM_II)
+        return B.n > 1 ? B.ntiles[l] > 0 : !use_resident(p, geom_of(B.pl[0], l));
+    return B.n > 1 ? B.nres[l] < B.n : !use_resident(p, geom_of(B.pl[0], l));
 }
 
-// The strip height level l runs with (streamed levels only).
+// The strip height (ADMM) or block height (pDR, ALG1) level l runs with (tunable levels only).
 int level_rows(const Batch &B, int l) {
     if (B.n > 1 || B.tile_h[l] > 0) return B.tile_h[l];
     return admm_fused_tile_h(geom_of(B.pl[0], l), B.pl[0].prec != PREC_F32);
@@ -946,9 +943,10 @@ std::string tune_key(const Batch &B, const of_params *p, int l) {
     return k;
 }
 
-// One inner iteration of level l on the streaming kernel, as the solve launches it (storage
+// One inner iteration of level l on its per-iteration kernel, as the solve launches it (storage
 // precision of the level's main warps; no stop flag, no residual partials).
 void launch_level_iteration(of_ctx *ctx, const Batch &B, const of_params *p, int l, int parity, cudaStream_t s) {
+    const bool pdr = p->method == OF_PDR, cp = p->method == OF_CP;
     IterArgs a{};
     a.k = coefs_of(p);
     a.tile_h = B.tile_h[l];
@@ -957,34 +955,54 @@ void launch_level_iteration(of_ctx *ctx, const Batch &B, const of_params *p, int
         char *A = ctx->arena + B.base[0];
         const Fields b0 = fields_at(A + pl.stA, pl.planeS), b1 = fields_at(A + pl.stB, pl.planeS);
         a.g = geom_of(pl, l);
-        a.in = parity ? b1 : b0;
-        a.out = parity ? b0 : b1;
+        a.in = parity && !pdr ? b1 : b0;
+        a.out = pdr ? b0 : (parity ? b0 : b1);  // pDR works in place
         a.Ix = A + pl.data;
         a.Iy = A + pl.data + pl.planeT;
         a.It = A + pl.data + 2 * pl.planeT;
         a.ms_max = &((Misc *)(A + pl.misc))->ms_max;
+        a.tmp = (float *)(A + pl.tmp);
     } else {
         a.pairs = (const PairIter *)(ctx->arena + B.table_off + B.pairs_off[l][0]);
-        a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
-        a.ntiles = B.ntiles[l];
-        a.parity = parity;
+        if (pdr || cp) {
+            a.g = B.gmax[l];
+            a.ntiles = B.n - B.nres[l];
+            a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
+            a.parity = pdr ? 0 : parity;
+        } else {
+            a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
+            a.ntiles = B.ntiles[l];
+            a.parity = parity;
+        }
     }
-    launch_admm_fused(a, B.pl[0].prec, B.pl[0].pflow, s);
+    if (pdr) launch_pdr_fused(a, B.pl[0].prec, B.pl[0].pflow, s);
+    else if (cp) launch_cp(a, B.pl[0].prec, B.pl[0].pflow, s);
+    else launch_admm_fused(a, B.pl[0].prec, B.pl[0].pflow, s);
 }
 
-// Times every strip height on level l (2 untimed and 6 timed iterations each, CUDA events on the
-// context's own stream) and returns the fastest; ties keep the lower height.
+// Times every candidate shape on level l -- the strip heights of the streaming ADMM kernel, or the
+// block heights of the pDR / ALG1 kernels -- (2 untimed and 6 timed iterations each, CUDA events
+// on the context's own stream) and returns the fastest; ties keep the lower one.
 of_status tune_level(of_ctx *ctx, Batch &B, const of_params *p, int l, int *best) {
-    static const int cand[4] = {1, 2, 8, 32};
+    static const int cand_admm[4] = {1, 2, 8, 32}, cand_blocks[3] = {4, 8, 16};
+    const bool blocks = p->method == OF_PDR || p->method == OF_CP;
+    const int *cand = blocks ? cand_blocks : cand_admm;
+    const int ncand = blocks ? 3 : 4;
     constexpr int WARM = 2, REPS = 6;
     of_params q = *p;
     q.tol = 0.0;  // tables without stop flags: every timed launch does the full iteration
     ctx->tables_key.clear();  // from here on the arena's tables are the candidates' (also on error)
+    if (B.n > 1 && blocks) {  // the pair descriptors of the batched launches (any block height)
+        of_status st = upload_tables(ctx, B, &q);
+        ctx->tables_key.clear();
+        if (st != OF_OK) return st;
+    }
     float best_ms = 0.f;
     *best = 0;
-    for (int ty : cand) {
+    for (int c = 0; c < ncand; ++c) {
+        const int ty = cand[c];
         B.tile_h[l] = ty;
-        if (B.n > 1) {
+        if (B.n > 1 && !blocks) {
             B.ntiles[l] = batch_tiles(B, l, ty);
             of_status st = upload_tables(ctx, B, &q);
             ctx->tables_key.clear();
@@ -1007,14 +1025,14 @@ of_status tune_level(of_ctx *ctx, Batch &B, const of_params *p, int l, int *best
     return OF_OK;
 }
 
-// rows_per_warp = -1: sets B's strip heights from the context's tuning, timing the levels not
-// tuned yet.  The timing launches run on the arena (state and data zeroed first; the solve
+// rows_per_warp = -1: sets B's strip (or block) heights from the context's tuning, timing the
+// levels not tuned yet.  The timing launches run on the arena (state and data zeroed first; the solve
 // overwrites them) after a device synchronisation, so no queued solve still uses it.
 of_status resolve_rows(of_ctx *ctx, Batch &B, const of_params *p) {
     if (p->rows_per_warp != -1) return OF_OK;
     bool ready = false;
     for (int l = B.L - 1; l >= B.out_level; --l) {
-        if (!streamed_admm(B, p, l)) continue;
+        if (!tunable_level(B, p, l)) continue;
         const std::string key = tune_key(B, p, l);
         auto it = ctx->tuned.find(key);
         int ty = 0;
@@ -1038,7 +1056,7 @@ of_status resolve_rows(of_ctx *ctx, Batch &B, const of_params *p) {
             ctx->tuned[key] = ty;
         }
         B.tile_h[l] = ty;
-        if (B.n > 1) B.ntiles[l] = batch_tiles(B, l, ty);
+        if (B.n > 1 && block_height_of(p) == 0) B.ntiles[l] = batch_tiles(B, l, ty);
     }
     return OF_OK;
 }
@@ -1303,7 +1321,7 @@ of_status of_rows_per_warp(of_ctx *ctx, int n, const int *H, const int *W, const
         st = resolve_rows(ctx, B, params);
         if (st != OF_OK) return st;
     }
-    for (int l = 0; l < B.L; ++l) rows[l] = streamed_admm(B, params, l) ? level_rows(B, l) : 0;
+    for (int l = 0; l < B.L; ++l) rows[l] = tunable_level(B, params, l) ? level_rows(B, l) : 0;
     return OF_OK;
 }
 
@@ -1470,7 +1488,8 @@ namespace {
 // built-in rule picks for the actual width.
 int fields_partial_slots(int H, int pitch) {
     const Geom g{H, pitch, pitch};
-    return std::max({admm_fused_blocks(g, 1), admm_plain_blocks(g), pdr_plain_blocks(g), cp_blocks(g)});
+    return std::max({admm_fused_blocks(g, 1), admm_plain_blocks(g), pdr_plain_blocks(g, PARTIAL_ROWS_MIN),
+                     cp_blocks(g, PARTIAL_ROWS_MIN)});
 }
 
 }  // namespace

@@ -197,15 +197,19 @@ void launch_admm_plain(const IterArgs &a, cudaStream_t s);
 // geometry): blockIdx.z selects the pair, its planes are pairs[z].buf[0] and pairs[z].tmp, and
 // its partials occupy pdr_plain_blocks(args.g) slots starting at z * pdr_plain_blocks(args.g).
 int pdr_fused_blocks(Geom g);
+// Blocks of the pDR and ALG1 per-iteration kernels: 32 columns by tile_h rows (4, 8 or 16; any
+// other value means 8).  PARTIAL_ROWS_MIN is the smallest height, which launches the most blocks.
+constexpr int PARTIAL_ROWS_MIN = 4;
 // X and Xbar (w u v wb ub vb) in `prec_flow`, ybar and the data in `prec`.
 void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
-int pdr_plain_blocks(Geom g);
+int pdr_plain_blocks(Geom g, int tile_h = 8);
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------- ALG1 (k_cp.cu)
 // One fused kernel per iteration, reads args.in and writes args.out (ping-pong).  Batched form
 // as the pDR engines (blockIdx.z = pair, args.g = the largest geometry, parity selects buffers).
-int cp_blocks(Geom g);
+// For both, args.tile_h is the block height (see pdr_plain_blocks).
+int cp_blocks(Geom g, int tile_h = 8);
 void launch_cp(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 
 // ---------------------------------------------------------------- reductions (k_reduce.cu)

@@ -132,3 +132,38 @@ def test_rows_report_for_other_kernels(ctx):
     assert rows == [0, 8, 0]
     with pytest.raises(flow.OfError):
         flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(rows_per_warp=4))
+
+
+# ------------------------------------------------------------------ pDR / ALG1 block heights
+BLOCK_HEIGHTS = (4, 8, 16)
+
+
+@pytest.mark.parametrize("method", [2, 3])
+@pytest.mark.parametrize("beta", [0.05, 0.0])
+def test_pdr_and_alg1_block_heights_give_the_same_flow(ctx, method, beta):
+    """The pDR and ALG1 per-iteration kernels run blocks of 32 columns by 4, 8 or 16 rows (the
+    autotuner's choice): every height computes every pixel alike, so the flows are bitwise equal,
+    on a level with ragged right and bottom edges, single and batched."""
+    pr = synth.random_affine_rect_pair(203, 333, 21)
+    kw = dict(lam=2.0, levels=2, warps=2, iters=17, method=method, beta=beta, engine=STREAM)
+    ref = _solve(ctx, pr, rows_per_warp=0, **kw)
+    for h in BLOCK_HEIGHTS + (-1,):
+        got = _solve(ctx, pr, rows_per_warp=h, **kw)
+        assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), h
+        assert got[3]["iters_run"] == ref[3]["iters_run"]
+    P = flow.default_params(rows_per_warp=-1, **kw)
+    rows = flow.of_rows_per_warp(ctx, [pr.I0.shape], P)
+    assert all(r in BLOCK_HEIGHTS for r in rows), rows
+    pairs = [pr, synth.random_affine_rect_pair(64, 96, 22), synth.random_affine_rect_pair(130, 100, 23)]
+    for h in (4, 16, -1):
+        Pb = flow.default_params(rows_per_warp=h, **kw)
+        us, vs, _ = flow.of_solve_batch(ctx, [cu(p.I0) for p in pairs], [cu(p.I1) for p in pairs], Pb)
+        assert torch.equal(us[0], ref[0]) and torch.equal(vs[0], ref[1]), h
+
+
+def test_block_heights_are_validated_per_method(ctx):
+    pr = synth.sinusoid_pair()
+    for method, bad in ((2, 2), (3, 32), (0, 4), (1, 16)):
+        with pytest.raises(flow.OfError) as e:
+            _solve(ctx, pr, method=method, rows_per_warp=bad)
+        assert e.value.status == flow.OF_EINVAL
