@@ -529,7 +529,7 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
         for rid, k in warm:
             while flow.of_server_poll(ctx, rid, k) is None:
                 time.sleep(0.001)
-        pending, lat, done_at = {}, [], []
+        pending, lat, done_at, lat_size = {}, [], [], {}
         t0 = time.perf_counter()
         nxt = 0
         while (nxt < len(arrivals) or pending) and time.perf_counter() - t0 < duration_s + drain_s:
@@ -542,6 +542,7 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
                 r = flow.of_server_poll(ctx, rid, pending[rid])
                 if r is not None:
                     lat.append(r[2])
+                    lat_size.setdefault(pending[rid], []).append(r[2])
                     done_at.append(time.perf_counter() - t0)
                     del pending[rid]
             time.sleep(0.0005)
@@ -560,6 +561,9 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
             "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
             "gpix_iter_per_s": work / 1e3 / (done_at[-1] if done_at else 1.0), "max_active": max_active,
+            "p50_p99_ms_by_size": {"%dx%d" % (w, h): [round(float(np.percentile(v, 50)), 1),
+                                                      round(float(np.percentile(v, 99)), 1), len(v)]
+                                   for (h, w), v in sorted(lat_size.items())},
             "single_pair_path": {"value": len(sizes) / seq_s, "unit": "flows/s",
                                  "note": "the same requests through one of_solve at a time (device time)",
                                  "ms_per_solve": {"%dx%d" % (w, h): round(v, 3) for (h, w), v in single_ms.items()}}}

@@ -124,10 +124,13 @@ def test_autotuned_single_pair(ctx):
 
 
 def test_rows_report_for_other_kernels(ctx):
-    """Levels that do not run on the streaming ADMM kernel report 0: pDR, ALG1, the plain engine,
-    and levels below out_level."""
-    for kw in (dict(method=flow.OF_PDR), dict(method=flow.OF_CP), dict(engine=flow.OF_ENGINE_PLAIN)):
-        assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, **kw)) == [0, 0, 0]
+    """pDR and ALG1 report the block height of their per-iteration kernels on the levels they
+    stream (8 by default) and 0 on the level-resident one; the plain engine and levels below
+    out_level report 0."""
+    for kw in (dict(method=flow.OF_PDR), dict(method=flow.OF_CP)):
+        assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, **kw)) == [8, 8, 0]
+    plain = flow.default_params(levels=3, engine=flow.OF_ENGINE_PLAIN)
+    assert flow.of_rows_per_warp(ctx, [(480, 640)], plain) == [0, 0, 0]
     rows = flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, out_level=1, rows_per_warp=8))
     assert rows == [0, 8, 0]
     with pytest.raises(flow.OfError):
