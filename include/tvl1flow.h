@@ -123,6 +123,20 @@ typedef struct {
                             decision taken on it) can differ in the last FP32 digits.  Used by
                             of_solve and of_solve_batch; the step-level entry points and the
                             serving loop use the built-in choice.                             */
+    int c_adapt_iters;   /* ADMM methods, opt-in (an extension, not in the paper): 0 = the fixed
+                            step c of Sec. 4.  K > 0 (a multiple of 10): in the first warp of
+                            every pyramid level, after each 10th of its first K inner
+                            iterations, c is rescaled by residual balancing: with r the
+                            constraint residual ||A s + B y|| and d the dual residual of the
+                            preconditioned ADMM, c(B^*A ds - (a I - B^*B) dy, (M_s - a~) ds)
+                            (ds, dy: the change of s and y over the iteration), c is doubled
+                            when r > 10 d and halved when d > 10 r.  After those K iterations c
+                            is frozen for the rest of the level (its fixed-metric convergence,
+                            Prop. 3.1, applies from there on); the next finer level starts its
+                            window from that value.  The stopping test (tol) starts after the
+                            window.  Single pairs (of_solve, of_solve_host, n = 1) on the fused
+                            engines only: OF_EINVAL for pDR, ALG1, the plain engine, batches,
+                            the serving loop and the step-level entry points.                  */
 } of_params;
 
 typedef struct {
@@ -132,12 +146,14 @@ typedef struct {
     double energy;       /* primal energy eq. (l1:finite) at the output level's last linearisation */
     double dual_value;   /* <It, s> (eq. dual:l1:flow:cons); NaN for pDR and ALG1               */
     float ms;            /* device time of the solve in milliseconds                            */
+    float c;             /* ADMM step c at the end of the solve (params->c unless c_adapt_iters) */
 } of_stats;
 
 /* Fills p with the paper's Sec. 4 settings: pADMM (r = 1), c = 0.05, a = 8, a~ = max M_s,
  * rho = 1.9, sigma = 2, tau = 0.4, beta = 0.05, one SRBGS sweep; lambda = 0.05; eta = 0.5,
  * 3 levels, 5 warps, 50 iterations; FP32, fused engine; with 16-bit storage, the last warp
- * and the flow fields in FP32; the built-in strip heights (rows_per_warp = 0). */
+ * and the flow fields in FP32; the built-in strip heights (rows_per_warp = 0); fixed c
+ * (c_adapt_iters = 0). */
 void of_default_params(of_params *p);
 
 /* Creates a context on CUDA device `device`.  The context owns one device arena that grows on

@@ -67,12 +67,13 @@ class _Params(ctypes.Structure):
                 ("tau", ctypes.c_double), ("gs_sweeps", ctypes.c_int), ("eta", ctypes.c_double),
                 ("levels", ctypes.c_int), ("warps", ctypes.c_int), ("iters", ctypes.c_int),
                 ("tol", ctypes.c_double), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_double),
-                ("cp_sigma", ctypes.c_double), ("a_tilde_mode", ctypes.c_int)]
+                ("cp_sigma", ctypes.c_double), ("a_tilde_mode", ctypes.c_int), ("c_adapt_iters", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_longlong), ("residual", ctypes.c_double),
-                ("energy", ctypes.c_double), ("dual_value", ctypes.c_double)]
+                ("energy", ctypes.c_double), ("dual_value", ctypes.c_double),
+                ("c_final", ctypes.c_double), ("adapt_margin", ctypes.c_double)]
 
 
 @dataclass
@@ -98,12 +99,13 @@ class Params:
     cp_tau: float = 0.1      # ALG1 dual step (Sec. 4)
     cp_sigma: float = 1.25   # ALG1 primal step 1 / (8 cp_tau) (Sec. 4, reading of the step rule)
     a_tilde_mode: int = 0    # 0: a~ = max M_s per warp (Prop. 3.1); 1: per-pixel a~_ij = M_s(ij)
+    c_adapt_iters: int = 0   # 0: fixed c; K: residual balancing of c in each level's first K iterations
 
     def _c(self) -> _Params:
         return _Params(self.method, self.lam, self.beta, self.c, self.a, self.a_tilde, self.r,
                        self.rho, self.sigma, self.tau, self.gs_sweeps, self.eta, self.levels,
                        self.warps, self.iters, self.tol, self.out_level, self.cp_tau, self.cp_sigma,
-                       self.a_tilde_mode)
+                       self.a_tilde_mode, self.c_adapt_iters)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -137,6 +139,10 @@ def lib():
             "orc_cp_step_flat": (d, [i, i, PP, _D, _D, _D, ctypes.POINTER(_Params)]),
             "orc_inner_flat": (ctypes.c_longlong, [i, i, PP, _D, _D, _D, d, ctypes.POINTER(_Params), i, _D]),
             "orc_solve": (i, [i, i, _D, _D, ctypes.POINTER(_Params), _D, _D, _D, ctypes.POINTER(_Stats)]),
+            "orc_adapt_rule": (d, [d, d, d]),
+            "orc_adapt_residuals_flat": (d, [i, i, PP, PP, _D, _D, d, d, ctypes.POINTER(_Params), _D, _D]),
+            "orc_inner_adapt_flat": (ctypes.c_longlong, [i, i, PP, _D, _D, _D, d, ctypes.POINTER(_Params), i, i,
+                                                         _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -324,6 +330,34 @@ def inner(state: State, Ix, Iy, It, a_tilde, params: Params, iters: int):
     return int(n), res.value
 
 
+def adapt_residuals(prev: State, cur: State, Ix, Iy, a_tilde, c, params: Params):
+    """Norms (||r||, ||d||) of the constraint and dual residuals of the ADMM step prev -> cur taken
+    with step c (the residual-balancing extension)."""
+    dat = [_f64(x) for x in (Ix, Iy)]
+    H, W = dat[0].shape
+    P = params._c()
+    rn, dn = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    lib().orc_adapt_residuals_flat(H, W, prev._ptrs(), cur._ptrs(), *[_p(x) for x in dat], a_tilde, c,
+                                   ctypes.byref(P), ctypes.byref(rn), ctypes.byref(dn))
+    return rn.value, dn.value
+
+
+def adapt_rule(c, r_norm, d_norm):
+    """The balancing rule: c doubled when ||r|| > 10 ||d||, halved when ||d|| > 10 ||r||."""
+    return lib().orc_adapt_rule(c, r_norm, d_norm)
+
+
+def inner_adapt(state: State, Ix, Iy, It, a_tilde, params: Params, iters: int, window: int, c: float):
+    """A level's first warp under the adaptive step; returns (iters_run, residual, c, margin)."""
+    dat = [_f64(x) for x in (Ix, Iy, It)]
+    H, W = dat[0].shape
+    P = params._c()
+    res, cc, mg = ctypes.c_double(0.0), ctypes.c_double(c), ctypes.c_double(float("inf"))
+    n = lib().orc_inner_adapt_flat(H, W, state._ptrs(), *[_p(x) for x in dat], a_tilde, ctypes.byref(P), iters,
+                                   window, ctypes.byref(cc), ctypes.byref(mg), ctypes.byref(res))
+    return int(n), res.value, cc.value, mg.value
+
+
 def energy(w, u, v, Ix, Iy, It, beta, lam):
     arrs = [_f64(x) for x in (w, u, v, Ix, Iy, It)]
     H, W = arrs[0].shape
@@ -347,5 +381,6 @@ def solve(I0, I1, params: Params):
     rc = lib().orc_solve(H, W, _p(I0), _p(I1), ctypes.byref(P), _p(u), _p(v), _p(wo), ctypes.byref(st))
     if rc != 0:
         raise ValueError("oracle rejected the parameters")
-    stats = dict(iters_run=st.iters_run, residual=st.residual, energy=st.energy, dual_value=st.dual_value)
+    stats = dict(iters_run=st.iters_run, residual=st.residual, energy=st.energy, dual_value=st.dual_value,
+                 c_final=st.c_final, adapt_margin=st.adapt_margin)
     return u, v, wo, stats

@@ -312,6 +312,8 @@ typedef struct {
     double cp_tau;     /* ALG1 dual step */
     double cp_sigma;   /* ALG1 primal step */
     int a_tilde_mode;  /* 0: one a~ per warp (the paper's ||M_s||); 1: per-pixel a~_ij = M_s(ij) */
+    int c_adapt_iters; /* 0: fixed c; K > 0: residual balancing of c in the first K iterations of
+                          every level's first warp, c frozen afterwards (an extension) */
 } orc_params;
 
 typedef struct {
@@ -326,6 +328,9 @@ typedef struct {
 typedef struct {
     long long iters_run;
     double residual, energy, dual_value;
+    double c_final;      /* ADMM step c at the end of the solve */
+    double adapt_margin; /* smallest |log| distance of a balancing test from its thresholds
+                            (HUGE_VAL when no test ran): how far each decision was from a tie */
 } orc_stats;
 
 static double *orc_alloc(size_t n) { return (double *)calloc(n, sizeof(double)); }
@@ -624,6 +629,84 @@ double orc_dual_value(size_t n, const double *It, const double *s)
     return acc;
 }
 
+/* ------------------------------------------------------------------------------------- */
+/* Residual balancing of the ADMM step c (an extension: the paper keeps c fixed).  The    */
+/* stepsize conditions (eq. stepsize:constraint, Prop. 3.1) bound only a and a~, so every  */
+/* c > 0 keeps the proximal metrics c(aI - grad grad^*) and c(a~ - M_s) positive           */
+/* semidefinite, and the multipliers are unscaled, so c may change between iterations.     */
+/* Residuals after the step prev -> cur of eq. (aug:pre1:vector), from the optimality      */
+/* conditions of its two subproblems (B^*A ds = grad(beta ds), grad(Ix ds), grad(Iy ds);   */
+/* B^*B = grad grad^* = -grad div per component):                                          */
+/*   primal   r = A s + B y                     = (beta s - div p, Ix s - div q1, Iy s - div q2) */
+/*   dual     d_y = c(B^*A ds - (aI - B^*B) dy) = c(grad(A_k ds) - a dy_k - grad div dy_k)  */
+/*            d_s = c(M_s - a~) ds                                                          */
+/* Reading: the same residuals serve rpADMMI with r != 1 and rpADMMII.                      */
+/* ------------------------------------------------------------------------------------- */
+
+void orc_adapt_residuals(int H, int W, const orc_state *prev, const orc_state *cur, const double *Ix,
+                         const double *Iy, double a_tilde, double c, const orc_params *P, double *r_norm,
+                         double *d_norm)
+{
+    size_t N = (size_t)H * (size_t)W;
+    int has_w = P->beta != 0.0;
+    double a = P->a, beta = P->beta;
+    double *d = orc_alloc(N), *gx = orc_alloc(N), *gy = orc_alloc(N), *hx = orc_alloc(N), *hy = orc_alloc(N);
+    double *ds = orc_alloc(N), *t = orc_alloc(N), *e1 = orc_alloc(N), *e2 = orc_alloc(N);
+    double r2 = 0.0, d2 = 0.0;
+
+    /* primal residual at cur */
+    for (int comp = has_w ? 0 : 1; comp < 3; ++comp) {
+        const double *x = comp == 0 ? cur->p1 : comp == 1 ? cur->q11 : cur->q21;
+        const double *y = comp == 0 ? cur->p2 : comp == 1 ? cur->q12 : cur->q22;
+        orc_div(H, W, x, y, d);
+        for (size_t k = 0; k < N; ++k) {
+            double ak = comp == 0 ? beta : comp == 1 ? Ix[k] : Iy[k];
+            double rk = ak * cur->s[k] - d[k];
+            r2 += rk * rk;
+        }
+    }
+    /* dual residual, y block: one 2-vector dual per component (p; q1; q2) */
+    for (size_t k = 0; k < N; ++k) ds[k] = cur->s[k] - prev->s[k];
+    for (int comp = has_w ? 0 : 1; comp < 3; ++comp) {
+        const double *xc = comp == 0 ? cur->p1 : comp == 1 ? cur->q11 : cur->q21;
+        const double *yc = comp == 0 ? cur->p2 : comp == 1 ? cur->q12 : cur->q22;
+        const double *xp = comp == 0 ? prev->p1 : comp == 1 ? prev->q11 : prev->q21;
+        const double *yp = comp == 0 ? prev->p2 : comp == 1 ? prev->q12 : prev->q22;
+        for (size_t k = 0; k < N; ++k) {
+            e1[k] = xc[k] - xp[k];
+            e2[k] = yc[k] - yp[k];
+            t[k] = (comp == 0 ? beta : comp == 1 ? Ix[k] : Iy[k]) * ds[k]; /* A_comp ds */
+        }
+        orc_grad(H, W, t, hx, hy);  /* B^*A ds, this component */
+        orc_div(H, W, e1, e2, d);
+        orc_grad(H, W, d, gx, gy);  /* grad div dy = -B^*B dy */
+        for (size_t k = 0; k < N; ++k) {
+            double dx = c * (hx[k] - a * e1[k] - gx[k]);
+            double dy = c * (hy[k] - a * e2[k] - gy[k]);
+            d2 += dx * dx + dy * dy;
+        }
+    }
+    /* dual residual, s block */
+    for (size_t k = 0; k < N; ++k) {
+        double ms = beta * beta + Ix[k] * Ix[k] + Iy[k] * Iy[k];
+        double at = P->a_tilde_mode == 1 ? (ms > 1e-12 ? ms : 1e-12) : a_tilde;
+        double dk = c * (ms - at) * ds[k];
+        d2 += dk * dk;
+    }
+    free(d); free(gx); free(gy); free(hx); free(hy); free(ds); free(t); free(e1); free(e2);
+    *r_norm = sqrt(r2);
+    *d_norm = sqrt(d2);
+}
+
+/* The balancing rule: c doubled when ||r|| > 10 ||d||, halved when ||d|| > 10 ||r||,
+ * kept otherwise (residual balancing with mu = 10 and factor 2). */
+double orc_adapt_rule(double c, double r_norm, double d_norm)
+{
+    if (r_norm > 10.0 * d_norm) return 2.0 * c;
+    if (d_norm > 10.0 * r_norm) return 0.5 * c;
+    return c;
+}
+
 /* Runs `iters` inner iterations at one linearisation; the stopping test of the schedule
  * (residual < tol, checked every 10 iterations) applies when tol > 0.  Returns iterations
  * run; *res_out gets the last residual sqrt(||.||^2 / n_rows). */
@@ -645,6 +728,48 @@ long long orc_inner(int H, int W, orc_state *st, const double *Ix, const double 
     return k;
 }
 
+/* The first warp of a level under the adaptive step: the first `window` iterations run
+ * without the stopping test and rebalance c after every 10th (residuals of that iteration,
+ * with the c it used); the remaining iterations run with c frozen, their stopping test counted
+ * from the window's end.  *c carries the step in and out; *margin is lowered to the smallest
+ * |log| distance of a test from its two thresholds. */
+long long orc_inner_adapt(int H, int W, orc_state *st, const double *Ix, const double *Iy,
+                          const double *It, double a_tilde, const orc_params *P, int iters, int window,
+                          double *c, double *margin, double *res_out)
+{
+    size_t N = (size_t)H * (size_t)W;
+    double nrows = (double)N * (P->beta != 0.0 ? 3.0 : 2.0);
+    orc_params Q = *P;
+    orc_state prev;
+    memset(&prev, 0, sizeof(prev));
+    double **yk[7] = {&prev.p1, &prev.p2, &prev.q11, &prev.q12, &prev.q21, &prev.q22, &prev.s};
+    double *ys[7] = {st->p1, st->p2, st->q11, st->q12, st->q21, st->q22, st->s};
+    for (int f = 0; f < 7; ++f) *yk[f] = orc_alloc(N);
+    int kw = window < iters ? window : iters;
+    double res = 0.0;
+    for (int k = 0; k < kw; ++k) {
+        int test = (k + 1) % 10 == 0;
+        Q.c = *c;
+        if (test)
+            for (int f = 0; f < 7; ++f) memcpy(*yk[f], ys[f], N * sizeof(double));
+        res = sqrt(orc_admm_step(H, W, st, Ix, Iy, It, a_tilde, &Q) / nrows);
+        if (test) {
+            double rn, dn;
+            orc_adapt_residuals(H, W, &prev, st, Ix, Iy, a_tilde, *c, P, &rn, &dn);
+            double m1 = fabs(log(rn / (10.0 * dn))), m2 = fabs(log(dn / (10.0 * rn)));
+            if (m1 < *margin) *margin = m1;
+            if (m2 < *margin) *margin = m2;
+            *c = orc_adapt_rule(*c, rn, dn);
+        }
+    }
+    for (int f = 0; f < 7; ++f) free(*yk[f]);
+    Q.c = *c;
+    long long n = kw;
+    if (iters > kw) n += orc_inner(H, W, st, Ix, Iy, It, a_tilde, &Q, iters - kw, &res);
+    if (res_out) *res_out = res;
+    return n;
+}
+
 /* ------------------------------------------------------------------------------------- */
 /* The whole schedule: pyramid, coarse-to-fine levels, warps, inner iterations.           */
 /* Reading (Sec. 4 gives no details): state is zero at the coarsest level; at each finer   */
@@ -658,6 +783,7 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
 {
     int L = P->levels;
     if (H < 1 || W < 1 || L < 1 || L > 32 || P->out_level < 0 || P->out_level >= L) return 1;
+    if (P->c_adapt_iters < 0 || P->c_adapt_iters % 10 != 0 || (P->c_adapt_iters > 0 && P->method >= 2)) return 2;
     int Hs[32], Ws[32];
     double *P0[32], *P1[32];
     Hs[0] = H; Ws[0] = W;
@@ -680,6 +806,8 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
     double *u0 = orc_alloc(Nmax), *v0 = orc_alloc(Nmax);
     long long total = 0;
     double res = 0.0, a_tilde = 1.0;
+    double c_cur = P->c, margin = HUGE_VAL; /* the step carries from level to level */
+    orc_params Q = *P;
 
     for (int l = L - 1; l >= P->out_level; --l) {
         int h = Hs[l], w = Ws[l];
@@ -705,7 +833,13 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
             memcpy(v0, st.v, n * sizeof(double));
             double msmax = orc_warp_linearise(h, w, P0[l], P1[l], I1x, I1y, u0, v0, P->beta, Ix, Iy, It);
             a_tilde = P->a_tilde > 0.0 ? P->a_tilde : (msmax > 1e-12 ? msmax : 1e-12);
-            total += orc_inner(h, w, &st, Ix, Iy, It, a_tilde, P, P->iters, &res);
+            if (P->c_adapt_iters > 0 && wp == 0) {
+                total += orc_inner_adapt(h, w, &st, Ix, Iy, It, a_tilde, P, P->iters, P->c_adapt_iters, &c_cur,
+                                         &margin, &res);
+            } else {
+                Q.c = c_cur;
+                total += orc_inner(h, w, &st, Ix, Iy, It, a_tilde, &Q, P->iters, &res);
+            }
         }
         if (l == P->out_level) {
             memcpy(u_out, st.u, n * sizeof(double));
@@ -716,6 +850,8 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
                 stats->residual = res;
                 stats->energy = orc_energy(h, w, st.w, st.u, st.v, Ix, Iy, It, P->beta, P->lambda);
                 stats->dual_value = P->method >= 2 ? NAN : orc_dual_value(n, It, st.s);
+                stats->c_final = c_cur;
+                stats->adapt_margin = margin;
             }
         }
     }
@@ -762,4 +898,24 @@ long long orc_inner_flat(int H, int W, double **fields, const double *Ix, const 
     orc_state st;
     orc_state_from(&st, fields);
     return orc_inner(H, W, &st, Ix, Iy, It, a_tilde, P, iters, res_out);
+}
+
+double orc_adapt_residuals_flat(int H, int W, double **prev_fields, double **cur_fields, const double *Ix,
+                                const double *Iy, double a_tilde, double c, const orc_params *P, double *r_norm,
+                                double *d_norm)
+{
+    orc_state prev, cur;
+    orc_state_from(&prev, prev_fields);
+    orc_state_from(&cur, cur_fields);
+    orc_adapt_residuals(H, W, &prev, &cur, Ix, Iy, a_tilde, c, P, r_norm, d_norm);
+    return *r_norm;
+}
+
+long long orc_inner_adapt_flat(int H, int W, double **fields, const double *Ix, const double *Iy,
+                               const double *It, double a_tilde, const orc_params *P, int iters, int window,
+                               double *c, double *margin, double *res_out)
+{
+    orc_state st;
+    orc_state_from(&st, fields);
+    return orc_inner_adapt(H, W, &st, Ix, Iy, It, a_tilde, P, iters, window, c, margin, res_out);
 }

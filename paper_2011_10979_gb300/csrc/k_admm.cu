@@ -51,7 +51,7 @@ __global__ void k_yupdate_plain(IterArgs A, const float *dp, const float *dq1, c
     auto gx = [&](const float *f) { return hx ? f[o + 1] - f[o] : 0.f; };
     auto gy = [&](const float *f) { return hy ? f[o + P] - f[o] : 0.f; };
     const float *s = F(F_S), *Ix = (const float *)A.Ix, *Iy = (const float *)A.Iy;
-    const float inv_a = 1.f / A.k.a, inv_c = 1.f / A.k.c, beta = A.k.beta;
+    const float inv_a = 1.f / A.k.a, inv_c = 1.f / c_of(A.k, A.ms_max), beta = A.k.beta;
     if (has_w) {
         float p1 = F(F_P1)[o] + gx(dp) * inv_a + (gx(F(F_W)) * inv_c - beta * gx(s)) * inv_a;
         float p2 = F(F_P2)[o] + gy(dp) * inv_a + (gy(F(F_W)) * inv_c - beta * gy(s)) * inv_a;
@@ -83,7 +83,7 @@ __global__ void k_supdate_plain(IterArgs A, const float *dp, const float *dq1, c
         const size_t o = (size_t)i * P + j;
         auto F = [&](int f) { return (float *)A.in.f[f]; };
         const float ix = ((const float *)A.Ix)[o], iy = ((const float *)A.Iy)[o], it = ((const float *)A.It)[o];
-        const float beta = A.k.beta, c = A.k.c, lam = A.k.lambda, rho = A.k.rho;
+        const float beta = A.k.beta, c = c_of(A.k, A.ms_max), lam = A.k.lambda, rho = A.k.rho;
         const float s_old = F(F_S)[o];
         float w = has_w ? F(F_W)[o] : 0.f, u = F(F_U)[o], v = F(F_V)[o];
         const float ms = beta * beta + ix * ix + iy * iy;

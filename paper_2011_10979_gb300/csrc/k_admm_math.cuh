@@ -8,25 +8,25 @@
 
 namespace tvl1 {
 
-// Step constants of one warp: 1/a, 1/c, beta, 1/a~, 1/(a~ c), c, lambda, rho, 1 - rho, r c, and
+// Step constants of one warp (c: the step of the iteration, c_of): 1/a, 1/c, beta, 1/a~, 1/(a~ c), c, lambda, rho, 1 - rho, r c, and
 // whether a~ is the per-pixel diagonal a~_ij = M_s(ij) instead of one value per warp.
 struct StepK {
     float inv_a, inv_c, beta, inv_at, inv_atc, cc, lam, rho, omr, rc;
     int per_pixel;
 };
 
-__device__ __forceinline__ StepK step_coefs(const Coefs &K, float at) {
+__device__ __forceinline__ StepK step_coefs(const Coefs &K, float at, float c) {
     StepK s;
     s.inv_a = 1.f / K.a;
-    s.inv_c = 1.f / K.c;
+    s.inv_c = 1.f / c;
     s.beta = K.beta;
     s.inv_at = 1.f / at;
-    s.inv_atc = 1.f / (at * K.c);
-    s.cc = K.c;
+    s.inv_atc = 1.f / (at * c);
+    s.cc = c;
     s.lam = K.lambda;
     s.rho = K.rho;
     s.omr = 1.f - K.rho;
-    s.rc = K.r * K.c;
+    s.rc = K.r * c;
     s.per_pixel = K.a_tilde_mode == 1;
     return s;
 }

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(roll::WARPS * 32, PERSIST_MIN_BLOCKS) k_admm_p
             src[7] = pp->Ix;
             src[8] = pp->Iy;
             src[9] = pp->It;
-            const StepK SK = step_coefs(A.k, a_tilde_of(A.k, pp->ms_max));
+            const StepK SK = step_coefs(A.k, a_tilde_of(A.k, pp->ms_max), c_of(A.k, pp->ms_max));
             const int r0 = (int)((long long)sg.t * H / sg.m), r1 = (int)((long long)(sg.t + 1) * H / sg.m);
             const int c0 = sg.sx * roll::SW - 2;
             const bool interior = c0 >= 1 && c0 + 32 <= W - 1 && r0 >= 2 && r1 <= H - 2;

@@ -102,7 +102,7 @@ __device__ __forceinline__ float strip(const void *const *src, void *const *dst,
     load_row<T, TF, HAS_W, INT>(n2, src, y0 - 1, c, H, W, P);
     // a~ (one device scalar of the warp) and the step coefficients after the first rows' loads
     // are in flight, so their latencies overlap
-    const StepK SK = skp ? *skp : step_coefs(K, a_tilde_of(K, msp));
+    const StepK SK = skp ? *skp : step_coefs(K, a_tilde_of(K, msp), c_of(K, msp));
 #pragma unroll UNROLL
     for (int k = 0; k < NROWS; ++k) {
         const int i = y0 - 2 + k;                 // row entering the window

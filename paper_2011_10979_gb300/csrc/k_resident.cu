@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(RT, 1) k_admm_resident(ResArgs A) {
         push_n(S_IX, li, j, ix);
         push_n(S_IY, li, j, iy);
     });
-    const StepK K = step_coefs(A.k, a_tilde_of(A.k, msp));
+    const StepK K = step_coefs(A.k, a_tilde_of(A.k, msp), c_of(A.k, msp));
     cl.sync();
 
     // div y at the band's pixels from y (west neighbour; north neighbour, for the first band row

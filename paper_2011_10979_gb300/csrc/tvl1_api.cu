@@ -68,7 +68,8 @@ Plan make_plan(int H, int W, const of_params *p) {
     for (int l = 0; l < pl.L; ++l) {
         const Geom g{pl.H[l], pl.W[l], pl.P[l]};
         mb = std::max({mb, admm_fused_blocks(g, p->rows_per_warp != 0 ? 1 : 0), admm_plain_blocks(g),
-                       pdr_plain_blocks(g, PARTIAL_ROWS_MIN), cp_blocks(g, PARTIAL_ROWS_MIN), energy_blocks(g)});
+                       pdr_plain_blocks(g, PARTIAL_ROWS_MIN), cp_blocks(g, PARTIAL_ROWS_MIN), energy_blocks(g),
+                       adapt_blocks(g)});
     }
     pl.max_blocks = mb;
     pl.partials = take(3 * (size_t)mb * sizeof(double));
@@ -95,6 +96,7 @@ Coefs coefs_of(const of_params *p) {
     k.a_tilde_mode = p->a_tilde_mode;
     k.method = p->method;
     k.gs_sweeps = p->gs_sweeps;
+    k.c_dev = p->c_adapt_iters > 0 ? 1 : 0;
     return k;
 }
 
@@ -167,6 +169,12 @@ of_status validate(const of_params *p, int H, int W) {
     if (p->engine == OF_ENGINE_PLAIN && p->precision != OF_PREC_FP32)
         return fail(OF_EINVAL, "the plain engine runs in FP32 only");
     if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
+    if (p->c_adapt_iters < 0 || p->c_adapt_iters % 10 != 0)
+        return fail(OF_EINVAL, "c_adapt_iters must be 0 or a positive multiple of 10");
+    if (p->c_adapt_iters > 0 && (p->method == OF_PDR || p->method == OF_CP))
+        return fail(OF_EINVAL, "c_adapt_iters applies to the ADMM methods only");
+    if (p->c_adapt_iters > 0 && p->engine == OF_ENGINE_PLAIN)
+        return fail(OF_EINVAL, "c_adapt_iters needs a fused engine (the plain engine iterates in place)");
     return OF_OK;
 }
 
@@ -654,6 +662,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             c.data32[d] = c.A + pl.data32 + d * pl.plane32;
         }
         cudaMemsetAsync(c.misc, 0, sizeof(Misc), s);
+        if (p->c_adapt_iters > 0) launch_c_init(&c.misc->c_cur, p->c, s);
         for (int l = 1; l < L; ++l) {
             launch_pyr_down((float *)(c.A + pl.img0[l - 1]), geom_of(pl, l - 1), (float *)(c.A + pl.img0[l]),
                             geom_of(pl, l), taps, (float *)(c.A + pl.blur), s);
@@ -724,18 +733,63 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 pflow = PREC_F32;
             }
             const int start = cur;
+            // adaptive step c (single pair, ADMM): the level's first warp runs its first
+            // c_adapt_iters iterations one streaming launch each and rebalances c after every
+            // 10th; the level's engine then runs the other `rest` iterations with c frozen
+            const int kw = (p->c_adapt_iters > 0 && wp == 0) ? std::min(p->c_adapt_iters, p->iters) : 0;
+            const int rest = p->iters - kw;
+            if (kw > 0) {
+                const PairCtx &c = pc[0];
+                const Geom g = geom_of(*c.pl, l);
+                const Fields *bf = bufs_of(c);
+                const void *const *dat = data_of(c);
+                const int mb = c.pl->max_blocks;
+                for (int it = 0; it < kw; ++it) {
+                    const bool final_it = last_warp && rest == 0 && it == kw - 1;
+                    IterArgs a{};
+                    a.k = k;
+                    a.g = g;
+                    a.in = bf[(start + it) & 1];
+                    a.out = bf[(start + it + 1) & 1];
+                    a.Ix = dat[0];
+                    a.Iy = dat[1];
+                    a.It = dat[2];
+                    a.ms_max = &c.misc->ms_max;
+                    a.partials = final_it ? c.partials : nullptr;
+                    a.tile_h = B.tile_h[l];
+                    launch_admm_fused(a, prec, pflow, s);
+                    if (final_it) launch_sum(c.partials, blocks_of(g, l), &c.misc->res_final, s);
+                    if ((it + 1) % 10 == 0) {
+                        AdaptArgs d{};
+                        d.g = g;
+                        d.k = k;
+                        d.prev = a.in;
+                        d.cur = a.out;
+                        d.Ix = dat[0];
+                        d.Iy = dat[1];
+                        d.ms_max = &c.misc->ms_max;
+                        d.c = &c.misc->c_cur;
+                        d.part_r = c.partials + mb;
+                        d.part_d = c.partials + 2 * mb;
+                        d.has_w = has_w;
+                        launch_adapt_c(d, prec, s);
+                    }
+                }
+                launch_count_iters(&c.misc->iters, nullptr, kw, s);
+            }
+            const int start2 = (start + kw) & 1;  // where the level's engine picks the state up
             // level-resident engine: the single pair, or the batch's resident pairs, in one launch
             const bool res1 = !batched && use_resident(p, geom_of(*pc[0].pl, l));
             const bool resb = batched && B.nres[l] > 0;
-            if (p->iters > 0 && (res1 || resb)) {
+            if (rest > 0 && (res1 || resb)) {
                 ResArgs r{};
                 r.k = k;
-                r.iters = p->iters;
+                r.iters = rest;
                 r.check = p->tol > 0.0;
                 r.final_res = last_warp;
                 r.tol = p->tol;
-                r.parity_in = start;
-                r.parity_out = pingpong ? (start + p->iters) & 1 : start;  // pDR works in place
+                r.parity_in = start2;
+                r.parity_out = pingpong ? (start2 + rest) & 1 : start2;  // pDR works in place
                 if (res1) {
                     const PairCtx &c = pc[0];
                     const Geom g = geom_of(*c.pl, l);
@@ -766,7 +820,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             // persistent engine: every inner iteration of the level's other pairs in one launch
             const bool persl = B.pers[l];
             char *T = ctx->arena + B.table_off;
-            if (persl && p->iters > 0) {
+            if (persl && rest > 0) {
                 const int N = (int)B.psegs[l].size();
                 cudaMemsetAsync(T + B.pctr_off[l], 0, sizeof(unsigned) * (N + n), s);
                 PersistArgs a{};
@@ -780,8 +834,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 a.flags = (unsigned *)(T + B.pctr_off[l]);
                 a.pbar = a.flags + N;
                 a.partials = (double *)(T + B.ppart_off[l]);
-                a.parity = start;
-                a.iters = p->iters;
+                a.parity = start2;
+                a.iters = rest;
                 a.check = p->tol > 0.0;
                 a.final_res = last_warp;
                 a.tol = p->tol;
@@ -790,9 +844,9 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
             // the non-resident pairs (ALG1)
             const bool streamed = !persl && (batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1);
-            for (int it = 0; streamed && it < p->iters; ++it) {
+            for (int it = 0; streamed && it < rest; ++it) {
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
-                const bool final_it = last_warp && it == p->iters - 1;
+                const bool final_it = last_warp && it == rest - 1;
                 IterArgs a{};
                 a.k = k;
                 if (!batched) {
@@ -801,8 +855,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     const Fields *bf = bufs_of(c);
                     const void *const *dat = data_of(c);
                     a.g = g;
-                    a.in = bf[pingpong ? (start + it) & 1 : start];
-                    a.out = bf[pingpong ? (start + it + 1) & 1 : start];
+                    a.in = bf[pingpong ? (start2 + it) & 1 : start2];
+                    a.out = bf[pingpong ? (start2 + it + 1) & 1 : start2];
                     a.Ix = dat[0];
                     a.Iy = dat[1];
                     a.It = dat[2];
@@ -833,21 +887,21 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         a.g = B.gmax[l];
                         a.ntiles = n - B.nres[l];
                         a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
-                        a.parity = start;
+                        a.parity = start2;
                         a.tile_h = B.tile_h[l];
                         launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
                         a.g = B.gmax[l];
                         a.ntiles = n - B.nres[l];
                         a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
-                        a.parity = (start + it) & 1;
+                        a.parity = (start2 + it) & 1;
                         a.tile_h = B.tile_h[l];
                         launch_cp(a, prec, pflow, s);
                     } else {
                         a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
                         a.ntiles = B.ntiles[l];
                         a.tile_h = B.tile_h[l];
-                        a.parity = (start + it) & 1;
+                        a.parity = (start2 + it) & 1;
                         launch_admm_fused(a, prec, pflow, s);
                     }
                     if (check)
@@ -857,22 +911,22 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             }
             const PairScalars *ps = batched ? (const PairScalars *)(ctx->arena + B.table_off + B.scal_off[l]) : nullptr;
             if (batched) {
-                launch_count_iters_batched(ps, n, p->tol > 0.0 ? p->iters % 10 : p->iters, p->tol > 0.0, s);
+                launch_count_iters_batched(ps, n, p->tol > 0.0 ? rest % 10 : rest, p->tol > 0.0, s);
             } else if (!res1) {
                 Misc *m = pc[0].misc;
-                if (p->tol > 0.0) launch_count_iters(&m->iters, &m->done, p->iters % 10, s);
-                else launch_count_iters(&m->iters, nullptr, p->iters, s);
+                if (p->tol > 0.0) launch_count_iters(&m->iters, &m->done, rest % 10, s);
+                else launch_count_iters(&m->iters, nullptr, rest, s);
             }
             if (pingpong) {
                 const int fin = (start + p->iters) & 1;
-                if (p->tol > 0.0 && (p->iters & 1))
+                if (p->tol > 0.0 && (rest & 1))
                     for (int q = 0; q < n; ++q)
                         if (!(res1 || (batched && B.res[l][q])))  // the resident engine writes buf[fin] itself
-                            launch_parity_fix(bufs_of(pc[q])[start], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l),
+                            launch_parity_fix(bufs_of(pc[q])[start2], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l),
                                               cp ? pflow : prec, pflow, &pc[q].misc->done, 1, s);
                 cur = fin;
             }
-            if (last_warp && p->iters > 0 && !res1) {
+            if (last_warp && rest > 0 && !res1) {
                 if (persl) {
                     double *pp = (double *)(T + B.ppart_off[l]);
                     if (batched)
@@ -949,6 +1003,7 @@ void launch_level_iteration(of_ctx *ctx, const Batch &B, const of_params *p, int
     const bool pdr = p->method == OF_PDR, cp = p->method == OF_CP;
     IterArgs a{};
     a.k = coefs_of(p);
+    a.k.c_dev = 0;  // timing only: the fixed parameter c, whatever the arena's device scalars hold
     a.tile_h = B.tile_h[l];
     if (B.n == 1) {
         const Plan &pl = B.pl[0];
@@ -1106,6 +1161,7 @@ of_status read_stats(of_ctx *ctx, const Batch &B, int q, const of_params *p, cud
     stats->residual = p->iters > 0 ? sqrt(m.res_final / rows) : 0.0;
     stats->energy = m.energy;
     stats->dual_value = (p->method == OF_PDR || p->method == OF_CP) ? NAN : m.dual;
+    stats->c = p->c_adapt_iters > 0 ? m.c_cur : p->c;
     if (m.timeout) return fail(OF_ETIMEOUT, "a bounded wait of the persistent engine ran out");
     if (!isfinite(stats->residual) || !isfinite(stats->energy))
         return fail(OF_ENUMERIC, "non-finite residual or energy (NaN/Inf in the inputs or parameters?)");
@@ -1144,6 +1200,7 @@ void of_default_params(of_params *p) {
     p->cp_tau = 0.1f;
     p->cp_sigma = 1.25f;
     p->a_tilde_mode = 0;
+    p->c_adapt_iters = 0;
 }
 
 of_status of_create(of_ctx **out, int device, size_t hbm_budget_bytes) {
@@ -1340,6 +1397,8 @@ of_status solve_pairs(of_ctx *ctx, int n, const float *const *I0, const float *c
     if (!params) return fail(OF_EINVAL, "params is NULL");
     if (n > 1 && params->engine == OF_ENGINE_PLAIN)
         return fail(OF_EINVAL, "batched solves use the fused engine (the plain engine is single-pair)");
+    if (n > 1 && params->c_adapt_iters != 0)
+        return fail(OF_EINVAL, "c_adapt_iters is supported for single-pair solves only");
     for (int q = 0; q < n; ++q) {
         of_status st = validate(params, H[q], W[q]);
         if (st != OF_OK) return st;
@@ -1514,6 +1573,8 @@ of_status iterate_common(of_fields f, const float *Ix, const float *Iy, const fl
     if (!params) return fail(OF_EINVAL, "params is NULL");
     of_status st = validate(params, H, W);
     if (st != OF_OK) return st;
+    if (params->c_adapt_iters != 0)
+        return fail(OF_EINVAL, "c_adapt_iters applies to whole solves, not to the step-level entry points");
     const int want = params->method == OF_PDR ? KIND_PDR : params->method == OF_CP ? KIND_CP : KIND_ADMM;
     if (want != kind) return fail(OF_EINVAL, "params->method does not match the entry point");
     const bool pdr = kind == KIND_PDR, cp = kind == KIND_CP, xb = pdr || cp;

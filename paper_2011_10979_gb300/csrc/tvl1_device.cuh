@@ -62,6 +62,10 @@ __device__ __forceinline__ float a_tilde_of(const Coefs &k, const float *ms_max)
     return m > 1e-12f ? m : 1e-12f;
 }
 
+// The ADMM step c of the current iteration: the parameter, or with an adaptive step the value the
+// solve keeps on the device directly before the pair's ms_max.
+__device__ __forceinline__ float c_of(const Coefs &k, const float *ms_max) { return k.c_dev ? ms_max[-1] : k.c; }
+
 }  // namespace tvl1
 
 #define TVL1_DISPATCH_PREC(prec, T, ...)                         \

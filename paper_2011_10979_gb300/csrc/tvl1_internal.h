@@ -34,6 +34,8 @@ struct Coefs {
     int a_tilde_mode;     // 0: a~ per warp; 1: per-pixel a~_ij = max(M_s(ij), 1e-12)
     int method;           // 0 rpADMMI, 1 rpADMMII, 2 pDR, 3 ALG1
     int gs_sweeps;
+    int c_dev;            // 1: c is the adapted value the solve keeps on the device, read at
+                          // ms_max[-1] (Misc::c_cur); 0: c above
 };
 
 // One pair at one level, for the batched (work-list) form of the fused engines: both ping-pong
@@ -232,6 +234,28 @@ void launch_count_iters_batched(const PairScalars *ps, int npairs, int n, bool u
 // state ((done && *done) ? 1 : 0) equals `want_done`.
 void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, int prec_flow, const int *done,
                        int want_done, cudaStream_t s);
+
+// ---------------------------------------------------------------- adaptive ADMM step (k_adapt.cu)
+// Residual balancing of c after one ADMM iteration prev -> cur (both state buffers intact): the
+// constraint residual ||A s + B y|| and the dual residual of the preconditioned ADMM, summed over
+// adapt_blocks(g) blocks into part_r / part_d, then c doubled (||r|| > 10 ||d||) or halved
+// (||d|| > 10 ||r||) in place.  Duals and data in `prec`; the flow fields are not read.
+constexpr int ADAPT_MAX_BLOCKS = 1216;
+struct AdaptArgs {
+    Geom g{};
+    Coefs k{};        // k.c_dev = 1: c is read at ms_max[-1] (== c below)
+    Fields prev{}, cur{};
+    const void *Ix = nullptr, *Iy = nullptr;
+    const float *ms_max = nullptr;
+    float *c = nullptr;
+    double *part_r = nullptr, *part_d = nullptr;  // adapt_blocks(g) slots each
+    int has_w = 0;
+};
+int adapt_blocks(Geom g);
+void launch_adapt_c(const AdaptArgs &a, int prec, cudaStream_t s);
+// *c = c0 (one thread): the adapted step starts from the parameter at the start of a solve.
+void launch_c_init(float *c, float c0, cudaStream_t s);
+
 // Whether field k is a flow/illumination plane (w u v wb ub vb), stored in the flow precision.
 __host__ __device__ inline bool is_flow_field(int k) { return k == F_W || k == F_U || k == F_V || k == F_WB || k == F_UB || k == F_VB; }
 

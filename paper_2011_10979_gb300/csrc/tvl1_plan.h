@@ -36,14 +36,19 @@ struct Plan {
     size_t total = 0;
 };
 
-// Device scalars at plan.misc.
+// Device scalars at plan.misc.  c_cur sits directly before ms_max: kernels that are handed a
+// pair's ms_max pointer read the adapted ADMM step c at ms_max[-1] (Coefs::c_dev); ms_max and
+// done are adjacent so that one 8-byte memset clears both at the start of a warp.
 struct Misc {
+    float c_cur;
     float ms_max;
     int done;
     long long iters;
     double res_check, res_final, energy, dual;
     int timeout;  // a bounded wait of the persistent engine ran out
 };
+static_assert(offsetof(Misc, ms_max) == offsetof(Misc, c_cur) + sizeof(float), "c_cur must precede ms_max");
+static_assert(offsetof(Misc, done) == offsetof(Misc, ms_max) + sizeof(float), "done must follow ms_max");
 
 // The arena layout of one H x W pair with these parameters (offsets from the pair's base).
 Plan make_plan(int H, int W, const of_params *p);

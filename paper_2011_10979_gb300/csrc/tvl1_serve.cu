@@ -337,6 +337,10 @@ of_status of_server_start(of_ctx *ctx, const of_params *params, size_t hbm_budge
         return OF_EINVAL;
     }
     if (of_arena_bytes(16, 16, params) == 0) return OF_EINVAL;  // validates the parameters
+    if (params->c_adapt_iters != 0) {
+        tvl1_set_error("of_server_start: c_adapt_iters is supported for single-pair solves only");
+        return OF_EINVAL;
+    }
     if (params->engine == OF_ENGINE_PLAIN) {
         tvl1_set_error("of_server_start: the serving loop batches on the fused kernels (not OF_ENGINE_PLAIN)");
         return OF_EINVAL;

@@ -43,12 +43,13 @@ class of_params(ctypes.Structure):
                 ("tol", ctypes.c_double), ("precision", ctypes.c_int), ("fp32_last_warp", ctypes.c_int),
                 ("fp32_flow", ctypes.c_int),
                 ("engine", ctypes.c_int), ("out_level", ctypes.c_int), ("cp_tau", ctypes.c_float),
-                ("cp_sigma", ctypes.c_float), ("a_tilde_mode", ctypes.c_int), ("rows_per_warp", ctypes.c_int)]
+                ("cp_sigma", ctypes.c_float), ("a_tilde_mode", ctypes.c_int), ("rows_per_warp", ctypes.c_int),
+                ("c_adapt_iters", ctypes.c_int)]
 
 
 class of_stats(ctypes.Structure):
     _fields_ = [("iters_run", ctypes.c_longlong), ("residual", ctypes.c_double), ("energy", ctypes.c_double),
-                ("dual_value", ctypes.c_double), ("ms", ctypes.c_float)]
+                ("dual_value", ctypes.c_double), ("ms", ctypes.c_float), ("c", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -117,8 +118,12 @@ def check(status, ctx=None):
 def default_params(**kw) -> of_params:
     p = of_params()
     lib().of_default_params(ctypes.byref(p))
+    names = {n for n, _ in of_params._fields_}
     for k, v in kw.items():
-        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+        k = "lambda_" if k in ("lam", "lambda") else k
+        if k not in names:
+            raise TypeError("unknown solver parameter %r" % k)
+        setattr(p, k, v)
     return p
 
 

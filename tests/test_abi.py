@@ -114,3 +114,19 @@ def test_fields_bytes_covers_every_width_up_to_the_pitch(L):
         need = 19 * plane + -(-(blocks * 8) // 256) * 256 + 64
         assert L.of_fields_bytes(H, pitch) >= need, (H, pitch)
     assert L.of_fields_bytes(0, 5) == 0 and L.of_fields_bytes(5, 0) == 0
+
+
+def test_adaptive_step_validation_without_gpu(L):
+    """c_adapt_iters: 0 (the fixed step) or a positive multiple of 10, ADMM methods on the fused
+    engines only."""
+    assert flow.default_params().c_adapt_iters == 0
+    for ok in (0, 10, 30, 1000):
+        q = flow.default_params(levels=5, c_adapt_iters=ok)
+        assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
+    for bad in (dict(c_adapt_iters=-10), dict(c_adapt_iters=15), dict(c_adapt_iters=20, method=flow.OF_PDR),
+                dict(c_adapt_iters=20, method=flow.OF_CP), dict(c_adapt_iters=20, engine=flow.OF_ENGINE_PLAIN)):
+        q = flow.default_params(levels=5, **bad)
+        assert L.of_arena_bytes(480, 640, ctypes.byref(q)) == 0, bad
+        assert b"c_adapt_iters" in L.of_last_error(None)
+    with pytest.raises(TypeError):
+        flow.default_params(c_adapt=20)
