@@ -112,8 +112,10 @@ typedef struct {
                             warp finishes per inner iteration; the strip is 29 columns wide):
                             0 = chosen per level from the level's size by the built-in rule;
                             1, 2, 8 or 32 = that height on every streamed level.
-                            pDR and ALG1: block height of their per-iteration kernels (blocks
-                            of 32 columns): 0 = 8; 4, 8 or 16 = that height.
+                            pDR with gs_sweeps > 1 and ALG1: block height of their per-iteration
+                            kernels (blocks of 32 columns): 0 = 8; 4, 8 or 16 = that height
+                            (pDR with one sweep runs one kernel of fixed 32 x 32 tiles per
+                            iteration and ignores it).
                             -1 = autotuned: the first solve of a layout on a context times every
                             height on each level that runs those kernels (a few iterations of the
                             real launch on the arena, after a device synchronisation) and keeps
@@ -179,7 +181,7 @@ long long of_solve_kernel_count(of_ctx *ctx, int H, int W, const of_params *para
  * per-iteration kernels) in a solve of n pairs of sizes H[k] x W[k] (n = 1: of_solve; n > 1:
  * of_solve_batch) with these parameters: rows[l] for l in [0, params->levels) is the height used on
  * pyramid level l, 0 where no pair of that level runs on those kernels (a level-resident or
- * persistent launch, the plain engine, or a level below out_level).  With params->rows_per_warp = -1 it runs the autotuner first if this layout is not
+ * persistent launch, pDR's one-launch tile kernel, the plain engine, or a level below out_level).  With params->rows_per_warp = -1 it runs the autotuner first if this layout is not
  * tuned on the context yet (allocating the arena and launching kernels; the device is
  * synchronised).  `rows` is caller-owned host memory of params->levels ints.  OF_EINVAL for bad
  * arguments, OF_ENOMEM / OF_ECUDA as for of_solve_batch. */

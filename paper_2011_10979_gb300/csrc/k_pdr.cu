@@ -11,6 +11,9 @@
 // between, and the last red half-sweep with the Xbar / ybar updates.
 #include <math.h>
 
+#include <mutex>
+#include <type_traits>
+
 #include "k_pdr_math.cuh"
 #include "tvl1_device.cuh"
 
@@ -281,6 +284,205 @@ __global__ void k_pdr_finish(IterArgs A) {
     }
 }
 
+// ---------------------------------------------------------------- one launch per iteration
+// The whole iteration (gs_sweeps = 1: red, black, red) for a 32 x 32 tile of output pixels in one
+// block, reading buffer `in` and writing buffer `out` (ping-pong, so no block reads what another
+// writes).  The chain of dependencies fixes the tile's halo: the ybar update needs X^{k+1} one
+// pixel east and south; X^{k+1} at a red pixel is its second red update, which needs black values
+// one pixel around, which need first red values one more pixel around, which need X^k (the old
+// black values) and b one more; b needs ybar one pixel west and north.  So the block stages, in
+// a 39 x 39 frame starting 3 pixels above and left of the tile, X^k on the whole frame, ybar on
+// offsets -3 .. 34 and Xbar on -2 .. 34, and runs the stages on shrinking regions between block
+// barriers: b and the first red half-sweep on -2 .. 34, black on -1 .. 34, the second red on
+// 0 .. 32, then the Xbar / ybar updates and the stores on the tile.  Each stage's arithmetic and
+// rounding (X rounded to its storage type after every half-sweep, b in FP32) is that of the
+// per-kernel engine, so the flows are bitwise equal; the residual's partial sums are grouped per
+// tile.
+constexpr int TT = 32, TFS = TT + 7, TFN = TFS * TFS, TNT = 512;
+enum { TX0 = 0, TB0 = 3, TY0 = 6, TXB0 = 12, TNPL = 15 };
+constexpr int TSMEM = TNPL * TFN * 4;
+
+template <typename T, typename TF, bool HAS_W>
+__global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
+    extern __shared__ float sm[];
+    __shared__ double red[32];
+    int H, W, P, pair = 0;
+    Fields in, out;
+    const void *Ixp, *Iyp, *Itp;
+    const int *donep;
+    if (A.pairs) {
+        pair = A.plist ? A.plist[blockIdx.z] : (int)blockIdx.z;
+        const PairIter *pp = A.pairs + pair;
+        const int4 gq = *reinterpret_cast<const int4 *>(&pp->g);
+        H = gq.x;
+        W = gq.y;
+        P = gq.z;
+        in = pp->buf[A.parity];
+        out = pp->buf[A.parity ^ 1];
+        Ixp = pp->Ix;
+        Iyp = pp->Iy;
+        Itp = pp->It;
+        donep = pp->done;
+    } else {
+        H = A.g.H;
+        W = A.g.W;
+        P = A.g.pitch;
+        in = A.in;
+        out = A.out;
+        Ixp = A.Ix;
+        Iyp = A.Iy;
+        Itp = A.It;
+        donep = A.done;
+    }
+    if (donep && *donep) return;  // uniform per block: the pair's warp met its stopping test
+    const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
+    if (i0 >= H || j0 >= W) {     // a tile of a smaller pair in a batched launch
+        if (A.partials && threadIdx.x == 0)
+            A.partials[(size_t)pair * gridDim.x * gridDim.y + blockIdx.x + gridDim.x * blockIdx.y] = 0.0;
+        return;
+    }
+    const int fi = i0 - 3, fj = j0 - 3;   // global coordinates of frame cell (0, 0)
+    const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
+    const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
+    const float sg = A.k.sigma, ta = A.k.tau, st = sg * ta;
+    constexpr int C0 = HAS_W ? 0 : 1;
+    auto S = [&](int k) { return sm + k * TFN; };
+    // frame cell x at offset (li - 3, lj - 3) from the tile's corner; the loops below visit the
+    // cells of a square of offsets [lo, hi] only
+    // the cells of the square of offsets [LO, HI] (compile-time bounds: no division at run time)
+    auto for_cells = [&](auto LO_, auto HI_, auto &&f) {
+        constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1;
+        for (int t = threadIdx.x; t < n * n; t += TNT) {
+            const int li = lo + 3 + t / n, lj = lo + 3 + t % n;
+            const int i = fi + li, j = fj + lj;
+            if (i >= 0 && i < H && j >= 0 && j < W) f(li * TFS + lj, i, j);
+        }
+    };
+    // ---- stage X^k (whole frame), ybar (offsets -3 .. 34), Xbar (-2 .. 34); zeros outside.  All
+    // of a thread's loads are issued before its shared-memory stores.
+    {
+        constexpr int NP = (TFN + TNT - 1) / TNT;
+        float v[NP][15];
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+            const int x = threadIdx.x + r * TNT;
+            const int li = x / TFS, lj = x % TFS;
+            const int i = fi + li, j = fj + lj;
+            const bool ok = x < TFN && i >= 0 && i < H && j >= 0 && j < W;
+            const bool oky = ok && li <= 37 && lj <= 37, okb = oky && li >= 1 && lj >= 1;
+            const size_t o = ok ? (size_t)i * P + j : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const bool on = c >= C0;
+                v[r][TX0 + c] = (ok && on) ? ldT<TF>(in.f[X[c]], o) : 0.f;
+                v[r][TY0 + 2 * c] = (oky && on) ? ldT<T>(in.f[Y1[c]], o) : 0.f;
+                v[r][TY0 + 2 * c + 1] = (oky && on) ? ldT<T>(in.f[Y2[c]], o) : 0.f;
+                v[r][TXB0 + c] = (okb && on) ? ldT<TF>(in.f[XB[c]], o) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NP; ++r) {
+            const int x = threadIdx.x + r * TNT;
+            if (x >= TFN) continue;
+#pragma unroll
+            for (int k = 0; k < 15; ++k)
+                if (k < TB0 || k >= TY0) S(k)[x] = v[r][k];
+        }
+    }
+    __syncthreads();
+    using I = int;
+    // ---- b = Xbar + sigma div ybar on offsets -2 .. 34
+    for_cells(std::integral_constant<I, -2>{}, std::integral_constant<I, 34>{}, [&](int x, int i, int j) {
+#pragma unroll
+        for (int c = C0; c < 3; ++c) {
+            const float *a = S(TY0 + 2 * c), *b = S(TY0 + 2 * c + 1);
+            const float d = (((j < W - 1 ? a[x] : 0.f) - (j > 0 ? a[x - 1] : 0.f)) + (i < H - 1 ? b[x] : 0.f)) -
+                            (i > 0 ? b[x - TFS] : 0.f);
+            S(TB0 + c)[x] = pdr_rhs(S(TXB0 + c)[x], d, sg);
+        }
+    });
+    __syncthreads();
+    // one Gauss-Seidel update of the pixels of colour `colour` (only those are visited) in the square
+    // of offsets [LO, HI], in place, rounded to the flow storage type
+    auto half_sweep = [&](auto LO_, auto HI_, int colour) {
+        constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1, hn = (n + 1) / 2;
+        for (int t = threadIdx.x; t < n * hn; t += TNT) {
+            const int r = t / hn, k = t % hn;
+            const int li = lo + 3 + r;
+            const int lj = lo + 3 + ((colour ^ (fi + li + fj + lo + 3)) & 1) + 2 * k;
+            if (lj > lo + 3 + n - 1) continue;
+            const int i = fi + li, j = fj + lj;
+            if (!(i >= 0 && i < H && j >= 0 && j < W)) continue;
+            const int x = li * TFS + lj;
+            const bool hw = j > 0, he = j < W - 1, hn_ = i > 0, hs = i < H - 1;
+            const int nb = (int)hw + (int)he + (int)hn_ + (int)hs;
+#pragma unroll
+            for (int c = C0; c < 3; ++c) {
+                const float *xc = S(TX0 + c);
+                float acc = 0.f;
+                if (hw) acc += xc[x - 1];
+                if (he) acc += xc[x + 1];
+                if (hn_) acc += xc[x - TFS];
+                if (hs) acc += xc[x + TFS];
+                S(TX0 + c)[x] = storage_round<TF>(pdr_gs(S(TB0 + c)[x], acc, nb, st));
+            }
+        }
+    };
+    half_sweep(std::integral_constant<I, -2>{}, std::integral_constant<I, 34>{}, 0);
+    __syncthreads();
+    half_sweep(std::integral_constant<I, -1>{}, std::integral_constant<I, 33>{}, 1);
+    __syncthreads();
+    half_sweep(std::integral_constant<I, 0>{}, std::integral_constant<I, 32>{}, 0);
+    __syncthreads();
+    // ---- the tile: Xbar and ybar updates, stores, residual ||X^{k+1} - X^k||^2
+    double res = 0.0;
+    const float beta = A.k.beta, lam = A.k.lambda;
+    for_cells(std::integral_constant<I, 0>{}, std::integral_constant<I, TT - 1>{}, [&](int x, int i, int j) {
+        const size_t o = (size_t)i * P + j;
+        const bool hx = j < W - 1, hy = i < H - 1;
+        float xv[3] = {0.f, 0.f, 0.f}, g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int c = C0; c < 3; ++c) {
+            const float *xc = S(TX0 + c);
+            xv[c] = xc[x];
+            g[2 * c] = hx ? xc[x + 1] - xv[c] : 0.f;
+            g[2 * c + 1] = hy ? xc[x + TFS] - xv[c] : 0.f;
+        }
+        const float ix = ldT<T>(Ixp, o), iy = ldT<T>(Iyp, o), it = ldT<T>(Itp, o);
+        float xb[3] = {S(TXB0)[x], S(TXB0 + 1)[x], S(TXB0 + 2)[x]};
+        pdr_xbar<HAS_W>(xv, xb, ix, iy, it, beta, lam, sg);
+        const float y[6] = {S(TY0)[x], S(TY0 + 1)[x], S(TY0 + 2)[x], S(TY0 + 3)[x], S(TY0 + 4)[x], S(TY0 + 5)[x]};
+        float yn[6];
+        pdr_ybar<HAS_W>(y, g, ta, yn);
+#pragma unroll
+        for (int c = C0; c < 3; ++c) {
+            stT<TF>(out.f[X[c]], o, xv[c]);
+            stT<TF>(out.f[XB[c]], o, xb[c]);
+            stT<T>(out.f[Y1[c]], o, yn[2 * c]);
+            stT<T>(out.f[Y2[c]], o, yn[2 * c + 1]);
+        }
+        const float dw = HAS_W ? xv[0] - ldT<TF>(in.f[F_W], o) : 0.f;
+        const float du = xv[1] - ldT<TF>(in.f[F_U], o), dv = xv[2] - ldT<TF>(in.f[F_V], o);
+        res += (double)dw * dw + (double)du * du + (double)dv * dv;
+    });
+    if (A.partials) {
+        const double tot = block_sum(res, red);
+        if (threadIdx.x == 0)
+            A.partials[(size_t)pair * gridDim.x * gridDim.y + blockIdx.x + gridDim.x * blockIdx.y] = tot;
+    }
+}
+
+template <typename T, typename TF> void launch_pdr_tile_t(const IterArgs &a, cudaStream_t s) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_pdr_tile<T, TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
+        cudaFuncSetAttribute(k_pdr_tile<T, TF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
+    });
+    dim3 grid((a.g.W + TT - 1) / TT, (a.g.H + TT - 1) / TT, a.pairs ? a.ntiles : 1);
+    if (a.k.beta != 0.f) k_pdr_tile<T, TF, true><<<grid, TNT, TSMEM, s>>>(a);
+    else k_pdr_tile<T, TF, false><<<grid, TNT, TSMEM, s>>>(a);
+}
+
 template <typename T, typename TF, bool HAS_W> void launch_pdr_w(const IterArgs &a, bool literal, cudaStream_t s) {
     const int py = literal ? PY_DEFAULT : block_rows(a.tile_h);
     dim3 grid((a.g.W + PX - 1) / PX, (a.g.H + py - 1) / py, a.pairs ? a.ntiles : 1), blk(PX, py);
@@ -322,7 +524,17 @@ int pdr_fused_blocks(Geom g) { return pdr_plain_blocks(g); }
 
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s) { launch_pdr_t<float, float>(a, true, s); }
 
+int pdr_tile_blocks(Geom g) { return ((g.W + TT - 1) / TT) * ((g.H + TT - 1) / TT); }
+
 void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
+    if (a.pdr_tile) {
+        if (prec == PREC_F32) launch_pdr_tile_t<float, float>(a, s);
+        else if (prec == PREC_F16 && prec_flow == PREC_F32) launch_pdr_tile_t<__half, float>(a, s);
+        else if (prec == PREC_F16) launch_pdr_tile_t<__half, __half>(a, s);
+        else if (prec_flow == PREC_F32) launch_pdr_tile_t<__nv_bfloat16, float>(a, s);
+        else launch_pdr_tile_t<__nv_bfloat16, __nv_bfloat16>(a, s);
+        return;
+    }
     if (prec == PREC_F32) launch_pdr_t<float, float>(a, false, s);
     else if (prec == PREC_F16 && prec_flow == PREC_F32) launch_pdr_t<__half, float>(a, false, s);
     else if (prec == PREC_F16) launch_pdr_t<__half, __half>(a, false, s);

@@ -270,6 +270,13 @@ struct Batch {
 // Whether a level of geometry g runs its inner iterations on the level-resident engine: the level
 // fits one cluster's shared memory and, with the default engine, is small enough for the resident
 // launch to beat the per-iteration kernels (all methods have a resident form).
+// pDR with one symmetric Gauss-Seidel sweep on the fused engines runs its non-resident levels on
+// the one-launch tile kernel (ping-pong buffers); more sweeps, the plain engine and the
+// stage-by-stage solver use the per-kernel engine (in place).
+bool pdr_tile_of(const of_params *p) {
+    return p->method == OF_PDR && p->engine != OF_ENGINE_PLAIN && p->gs_sweeps == 1;
+}
+
 bool use_resident(const of_params *p, Geom g) {
     if (!admm_resident_fits(g, p->method)) return false;
     return p->engine == OF_ENGINE_RESIDENT ||
@@ -578,7 +585,9 @@ of_status upload_tables(of_ctx *ctx, const Batch &B, const of_params *p) {
         int *rl = (int *)(img.data() + B.reslist_off[l]);
         int *sl = (int *)(img.data() + B.streamlist_off[l]);
         int t = 0, r = 0, ns = 0;
-        const int G = cp ? cp_blocks(B.gmax[l], B.tile_h[l]) : pdr_plain_blocks(B.gmax[l], B.tile_h[l]);
+        const int G = cp                ? cp_blocks(B.gmax[l], B.tile_h[l])
+                      : pdr_tile_of(p) ? pdr_tile_blocks(B.gmax[l])
+                                       : pdr_plain_blocks(B.gmax[l], B.tile_h[l]);
         for (int k = 0; k < B.n; ++k) {
             const Geom g = geom_of(B.pl[k], l);
             pair_iter(pi0, pi1, k, l);
@@ -627,10 +636,12 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
     const bool has_w = p->beta != 0.f;
     const bool pdr = p->method == OF_PDR, cp = p->method == OF_CP;
     const bool plain = p->engine == OF_ENGINE_PLAIN;
-    const bool pingpong = !pdr && !plain;  // ADMM fused engines and ALG1 read one buffer, write the other
+    const bool pdr_tile = pdr_tile_of(p);
+    // ADMM fused engines, ALG1 and the one-launch pDR kernel read one buffer and write the other
+    const bool pingpong = (!pdr && !plain) || pdr_tile;
     const GaussTaps taps = gauss_taps(p->eta);
     auto blocks_of = [&](Geom g, int l) {
-        return pdr ? pdr_plain_blocks(g, plain ? 0 : B.tile_h[l])
+        return pdr ? (pdr_tile ? pdr_tile_blocks(g) : pdr_plain_blocks(g, plain ? 0 : B.tile_h[l]))
                    : cp ? cp_blocks(g, B.tile_h[l]) : (plain ? admm_plain_blocks(g) : admm_fused_blocks(g, B.tile_h[l]));
     };
     const Coefs k = coefs_of(p);
@@ -865,6 +876,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     a.done = p->tol > 0.0 ? &c.misc->done : nullptr;
                     a.tmp = (float *)(c.A + c.pl->tmp);
                     a.tile_h = B.tile_h[l];
+                    a.pdr_tile = pdr_tile;
                     if (pdr) {
                         if (plain) launch_pdr_plain(a, s);
                         else launch_pdr_fused(a, prec, pflow, s);
@@ -887,8 +899,9 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         a.g = B.gmax[l];
                         a.ntiles = n - B.nres[l];
                         a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
-                        a.parity = start2;
+                        a.parity = pdr_tile ? (start2 + it) & 1 : start2;
                         a.tile_h = B.tile_h[l];
+                        a.pdr_tile = pdr_tile;
                         launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
                         a.g = B.gmax[l];
@@ -972,6 +985,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
 bool tunable_level(const Batch &B, const of_params *p, int l) {
     if (l < B.out_level || l >= B.L || B.pers[l]) return false;
     if (p->engine == OF_ENGINE_PLAIN || p->iters <= 0) return false;
+    if (pdr_tile_of(p)) return false;  // the one-launch pDR kernel has no block height to tune
     if (p->method == OF_PADMM_I || p->method == OF_PADMM_II)
         return B.n > 1 ? B.ntiles[l] > 0 : !use_resident(p, geom_of(B.pl[0], l));
     return B.n > 1 ? B.nres[l] < B.n : !use_resident(p, geom_of(B.pl[0], l));
@@ -1010,8 +1024,9 @@ void launch_level_iteration(of_ctx *ctx, const Batch &B, const of_params *p, int
         char *A = ctx->arena + B.base[0];
         const Fields b0 = fields_at(A + pl.stA, pl.planeS), b1 = fields_at(A + pl.stB, pl.planeS);
         a.g = geom_of(pl, l);
-        a.in = parity && !pdr ? b1 : b0;
-        a.out = pdr ? b0 : (parity ? b0 : b1);  // pDR works in place
+        const bool inplace = pdr && !pdr_tile_of(p);  // the per-kernel pDR engine works in place
+        a.in = parity && !inplace ? b1 : b0;
+        a.out = inplace ? b0 : (parity ? b0 : b1);
         a.Ix = A + pl.data;
         a.Iy = A + pl.data + pl.planeT;
         a.It = A + pl.data + 2 * pl.planeT;
@@ -1023,13 +1038,14 @@ void launch_level_iteration(of_ctx *ctx, const Batch &B, const of_params *p, int
             a.g = B.gmax[l];
             a.ntiles = B.n - B.nres[l];
             a.plist = (const int *)(ctx->arena + B.table_off + B.streamlist_off[l]);
-            a.parity = pdr ? 0 : parity;
+            a.parity = pdr && !pdr_tile_of(p) ? 0 : parity;
         } else {
             a.tiles = (const TileRef *)(ctx->arena + B.table_off + B.tiles_off[l]);
             a.ntiles = B.ntiles[l];
             a.parity = parity;
         }
     }
+    a.pdr_tile = pdr_tile_of(p);
     if (pdr) launch_pdr_fused(a, B.pl[0].prec, B.pl[0].pflow, s);
     else if (cp) launch_cp(a, B.pl[0].prec, B.pl[0].pflow, s);
     else launch_admm_fused(a, B.pl[0].prec, B.pl[0].pflow, s);

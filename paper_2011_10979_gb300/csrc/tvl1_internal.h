@@ -87,6 +87,9 @@ struct IterArgs {
     // ALG1 batched form: slice z of the grid works on pair plist[z] (the pairs of the level not on
     // the level-resident engine); its partials start at plist[z] * cp_blocks(g)
     const int *plist = nullptr;
+    // pDR, gs_sweeps = 1: the one-launch tile kernel, reading `in` and writing `out` (batched:
+    // buf[parity] -> buf[parity ^ 1]); 0: the per-kernel engine, in place in `in`
+    int pdr_tile = 0;
 };
 
 // Geometry of the fused ADMM engine: each warp owns a strip of admm_fused_strip_w() output
@@ -205,6 +208,8 @@ constexpr int PARTIAL_ROWS_MIN = 4;
 // X and Xbar (w u v wb ub vb) in `prec_flow`, ybar and the data in `prec`.
 void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s);
 int pdr_plain_blocks(Geom g, int tile_h = 8);
+// Blocks of the one-launch pDR tile kernel (32 x 32 output pixels each) on geometry g.
+int pdr_tile_blocks(Geom g);
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------- ALG1 (k_cp.cu)

@@ -124,11 +124,12 @@ def test_autotuned_single_pair(ctx):
 
 
 def test_rows_report_for_other_kernels(ctx):
-    """pDR and ALG1 report the block height of their per-iteration kernels on the levels they
-    stream (8 by default) and 0 on the level-resident one; the plain engine and levels below
-    out_level report 0."""
-    for kw in (dict(method=flow.OF_PDR), dict(method=flow.OF_CP)):
+    """ALG1 and pDR with two sweeps report the block height of their per-iteration kernels on the
+    levels they stream (8 by default) and 0 on the level-resident one; pDR with one sweep (its
+    one-launch tile kernel), the plain engine and levels below out_level report 0."""
+    for kw in (dict(method=flow.OF_PDR, gs_sweeps=2), dict(method=flow.OF_CP)):
         assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, **kw)) == [8, 8, 0]
+    assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, method=flow.OF_PDR)) == [0, 0, 0]
     plain = flow.default_params(levels=3, engine=flow.OF_ENGINE_PLAIN)
     assert flow.of_rows_per_warp(ctx, [(480, 640)], plain) == [0, 0, 0]
     rows = flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, out_level=1, rows_per_warp=8))
@@ -149,6 +150,8 @@ def test_pdr_and_alg1_block_heights_give_the_same_flow(ctx, method, beta):
     on a level with ragged right and bottom edges, single and batched."""
     pr = synth.random_affine_rect_pair(203, 333, 21)
     kw = dict(lam=2.0, levels=2, warps=2, iters=17, method=method, beta=beta, engine=STREAM)
+    if method == 2:
+        kw["gs_sweeps"] = 2  # one sweep runs the one-launch tile kernel, which has no height
     ref = _solve(ctx, pr, rows_per_warp=0, **kw)
     for h in BLOCK_HEIGHTS + (-1,):
         got = _solve(ctx, pr, rows_per_warp=h, **kw)
