@@ -285,25 +285,30 @@ __global__ void k_pdr_finish(IterArgs A) {
 }
 
 // ---------------------------------------------------------------- one launch per iteration
-// The whole iteration (gs_sweeps = 1: red, black, red) for a 32 x 32 tile of output pixels in one
+// The whole iteration (gs_sweeps = 1: red, black, red) for a TT x TT tile of output pixels in one
 // block, reading buffer `in` and writing buffer `out` (ping-pong, so no block reads what another
 // writes).  The chain of dependencies fixes the tile's halo: the ybar update needs X^{k+1} one
 // pixel east and south; X^{k+1} at a red pixel is its second red update, which needs black values
 // one pixel around, which need first red values one more pixel around, which need X^k (the old
 // black values) and b one more; b needs ybar one pixel west and north.  So the block stages, in
-// a 39 x 39 frame starting 3 pixels above and left of the tile, X^k on the whole frame, ybar on
-// offsets -3 .. 34 and Xbar on -2 .. 34, and runs the stages on shrinking regions between block
-// barriers: b and the first red half-sweep on -2 .. 34, black on -1 .. 34, the second red on
-// 0 .. 32, then the Xbar / ybar updates and the stores on the tile.  Each stage's arithmetic and
-// rounding (X rounded to its storage type after every half-sweep, b in FP32) is that of the
-// per-kernel engine, so the flows are bitwise equal; the residual's partial sums are grouped per
-// tile.
-constexpr int TT = 32, TFS = TT + 7, TFN = TFS * TFS, TNT = 512;
+// a (TT + 7)^2 frame starting 3 pixels above and left of the tile, X^k on the whole frame, ybar on
+// offsets -3 .. TT + 2 and Xbar on -2 .. TT + 2, and runs the stages on shrinking squares between
+// block barriers: b and the first red half-sweep on -2 .. TT + 2, black on -1 .. TT + 1, the
+// second red on 0 .. TT, then the Xbar / ybar updates and the stores on the tile.  Each stage's
+// arithmetic and rounding (X rounded to its storage type after every half-sweep, b in FP32) is
+// that of the per-kernel engine, so the flows are bitwise equal; the residual's partial sums are
+// grouped per tile.
+// Tiles of TT x TT output pixels: 32 (512 threads), or 16 (256 threads) on levels with fewer
+// 32-pixel tiles than SMs, where the larger tiles would leave most of the GPU idle.
 enum { TX0 = 0, TB0 = 3, TY0 = 6, TXB0 = 12, TNPL = 15 };
-constexpr int TSMEM = TNPL * TFN * 4;
+template <int TT> struct TileShape {
+    static constexpr int FS = TT + 7, FN = FS * FS, NT = TT == 32 ? 512 : 256, SMEM = TNPL * FN * 4;
+};
+int pdr_tile_size(Geom g) { return ((g.W + 31) / 32) * ((g.H + 31) / 32) < 152 ? 16 : 32; }
 
-template <typename T, typename TF, bool HAS_W>
-__global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
+template <typename T, typename TF, bool HAS_W, int TT>
+__global__ void __launch_bounds__(TileShape<TT>::NT) k_pdr_tile(IterArgs A) {
+    constexpr int TFS = TileShape<TT>::FS, TFN = TileShape<TT>::FN, TNT = TileShape<TT>::NT;
     extern __shared__ float sm[];
     __shared__ double red[32];
     int H, W, P, pair = 0;
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
             if (i >= 0 && i < H && j >= 0 && j < W) f(li * TFS + lj, i, j);
         }
     };
-    // ---- stage X^k (whole frame), ybar (offsets -3 .. 34), Xbar (-2 .. 34); zeros outside.  All
+    // ---- stage X^k (whole frame), ybar (offsets -3 .. TT + 2), Xbar (-2 .. TT + 2); zeros outside.  All
     // of a thread's loads are issued before its shared-memory stores.
     {
         constexpr int NP = (TFN + TNT - 1) / TNT;
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
             const int li = x / TFS, lj = x % TFS;
             const int i = fi + li, j = fj + lj;
             const bool ok = x < TFN && i >= 0 && i < H && j >= 0 && j < W;
-            const bool oky = ok && li <= 37 && lj <= 37, okb = oky && li >= 1 && lj >= 1;
+            const bool oky = ok && li <= TT + 5 && lj <= TT + 5, okb = oky && li >= 1 && lj >= 1;
             const size_t o = ok ? (size_t)i * P + j : 0;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -391,8 +396,8 @@ __global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
     }
     __syncthreads();
     using I = int;
-    // ---- b = Xbar + sigma div ybar on offsets -2 .. 34
-    for_cells(std::integral_constant<I, -2>{}, std::integral_constant<I, 34>{}, [&](int x, int i, int j) {
+    // ---- b = Xbar + sigma div ybar on offsets -2 .. TT + 2
+    for_cells(std::integral_constant<I, -2>{}, std::integral_constant<I, TT + 2>{}, [&](int x, int i, int j) {
 #pragma unroll
         for (int c = C0; c < 3; ++c) {
             const float *a = S(TY0 + 2 * c), *b = S(TY0 + 2 * c + 1);
@@ -428,11 +433,11 @@ __global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
             }
         }
     };
-    half_sweep(std::integral_constant<I, -2>{}, std::integral_constant<I, 34>{}, 0);
+    half_sweep(std::integral_constant<I, -2>{}, std::integral_constant<I, TT + 2>{}, 0);
     __syncthreads();
-    half_sweep(std::integral_constant<I, -1>{}, std::integral_constant<I, 33>{}, 1);
+    half_sweep(std::integral_constant<I, -1>{}, std::integral_constant<I, TT + 1>{}, 1);
     __syncthreads();
-    half_sweep(std::integral_constant<I, 0>{}, std::integral_constant<I, 32>{}, 0);
+    half_sweep(std::integral_constant<I, 0>{}, std::integral_constant<I, TT>{}, 0);
     __syncthreads();
     // ---- the tile: Xbar and ybar updates, stores, residual ||X^{k+1} - X^k||^2
     double res = 0.0;
@@ -472,15 +477,21 @@ __global__ void __launch_bounds__(TNT) k_pdr_tile(IterArgs A) {
     }
 }
 
-template <typename T, typename TF> void launch_pdr_tile_t(const IterArgs &a, cudaStream_t s) {
+template <typename T, typename TF, int TT> void launch_pdr_tile_tt(const IterArgs &a, cudaStream_t s) {
+    using TS = TileShape<TT>;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_pdr_tile<T, TF, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
-        cudaFuncSetAttribute(k_pdr_tile<T, TF, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TSMEM);
+        cudaFuncSetAttribute(k_pdr_tile<T, TF, true, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM);
+        cudaFuncSetAttribute(k_pdr_tile<T, TF, false, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, TS::SMEM);
     });
     dim3 grid((a.g.W + TT - 1) / TT, (a.g.H + TT - 1) / TT, a.pairs ? a.ntiles : 1);
-    if (a.k.beta != 0.f) k_pdr_tile<T, TF, true><<<grid, TNT, TSMEM, s>>>(a);
-    else k_pdr_tile<T, TF, false><<<grid, TNT, TSMEM, s>>>(a);
+    if (a.k.beta != 0.f) k_pdr_tile<T, TF, true, TT><<<grid, TS::NT, TS::SMEM, s>>>(a);
+    else k_pdr_tile<T, TF, false, TT><<<grid, TS::NT, TS::SMEM, s>>>(a);
+}
+
+template <typename T, typename TF> void launch_pdr_tile_t(const IterArgs &a, cudaStream_t s) {
+    if (pdr_tile_size(a.g) == 16) launch_pdr_tile_tt<T, TF, 16>(a, s);
+    else launch_pdr_tile_tt<T, TF, 32>(a, s);
 }
 
 template <typename T, typename TF, bool HAS_W> void launch_pdr_w(const IterArgs &a, bool literal, cudaStream_t s) {
@@ -524,7 +535,10 @@ int pdr_fused_blocks(Geom g) { return pdr_plain_blocks(g); }
 
 void launch_pdr_plain(const IterArgs &a, cudaStream_t s) { launch_pdr_t<float, float>(a, true, s); }
 
-int pdr_tile_blocks(Geom g) { return ((g.W + TT - 1) / TT) * ((g.H + TT - 1) / TT); }
+int pdr_tile_blocks(Geom g) {
+    const int tt = pdr_tile_size(g);
+    return ((g.W + tt - 1) / tt) * ((g.H + tt - 1) / tt);
+}
 
 void launch_pdr_fused(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
     if (a.pdr_tile) {
