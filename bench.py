@@ -188,9 +188,10 @@ def run_batch16(args):
 
 def run_level(args):
     """Single-level solves for a profiler: the 40x30 and 640x480 levels of the bench pair's kind
-    (one warp, 30 inner iterations, three solves each) on the given engine, strip height
-    --rows-per-warp (8 unless set).  A 40x30 level runs a handful of warps, each walking its strip
-    alone on its SM, so it shows the latency of one warp's row steps."""
+    (one warp, 30 inner iterations, three solves each) of --method (pADMM unless set) on the given
+    engine, strip height --rows-per-warp (8 unless set; ADMM only).  A 40x30 level runs a handful of
+    warps, each walking its strip alone on its SM, so it shows the latency of one warp's row steps;
+    with --method pdr the 640x480 level runs the one-launch pDR tile kernel."""
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -203,13 +204,14 @@ def run_level(args):
     for (h, w) in ((30, 40), (480, 640)):
         pr = synth.affine_rect_pair(h, w) if h >= 120 else synth.random_affine_rect_pair(h, w, 3)
         I0, I1 = torch.from_numpy(pr.I0).to(dev), torch.from_numpy(pr.I1).to(dev)
+        method = {"padmm": flow.OF_PADMM_I, "pdr": flow.OF_PDR, "alg1": flow.OF_CP}[args.method]
         P = flow.default_params(lam=LAM, beta=BETA, levels=1, warps=1, iters=30, engine=eng[args.engine],
-                                rows_per_warp=ty)
+                                method=method, rows_per_warp=ty if method == flow.OF_PADMM_I else 0)
         for _ in range(3):
             flow.of_solve(ctx, I0, I1, P, stats=False)
         torch.cuda.synchronize(dev)
     ctx.close()
-    print(json.dumps({"legs": "level", "engine": args.engine, "rows_per_warp": ty}))
+    print(json.dumps({"legs": "level", "method": args.method, "engine": args.engine, "rows_per_warp": ty}))
 
 
 def run_serving(args):
@@ -570,9 +572,9 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streaming pADMM kernel on the
-# 640 x 480 level (ncu, cold cache): 16.07 MB read + 4 KB written (the written planes stay in L2).
-# Set to None whenever that kernel changes, until it is captured again.
-ROLL_640_DRAM_BYTES = 16.07e6
+# 640 x 480 level (ncu, cold cache), for the strip height the built-in rule takes there.  Set to
+# None whenever that kernel changes, until it is captured again.
+ROLL_640_DRAM_BYTES = None
 
 
 def kernel_roofline(flow, torch, dev, pr, reps=20):
@@ -606,6 +608,8 @@ def kernel_roofline(flow, torch, dev, pr, reps=20):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t[iters] = e0.elapsed_time(e1) / reps / 1e3
+    ty = flow.of_rows_per_warp(ctx, [(H, W)], flow.default_params(lam=LAM, beta=BETA, levels=1,
+                                                                    engine=flow.OF_ENGINE_STREAM))[0]
     ctx.close()
     per = (t[220] - t[20]) / 200.0
     bytes_per_launch = 92.0 * H * W
@@ -613,7 +617,7 @@ def kernel_roofline(flow, torch, dev, pr, reps=20):
     # the level's working set stays in L2: its bandwidth for a working set of the same size
     # (half read, half written, streamed 400 times in one launch)
     l2 = flow.of_l2_bandwidth(int(bytes_per_launch), 400)
-    return {"kernel": "k_admm_roll<float,float,1,0,8> (640x480 level)", "bound": "hbm", "achieved": achieved,
+    return {"kernel": "k_admm_roll<float,float,1,0,%d> (640x480 level)" % ty, "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
             "traffic": ROLL_640_DRAM_BYTES, "us_per_launch": per * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch,
             "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 200",
@@ -634,6 +638,7 @@ def main():
     ap.add_argument("--legs", default="all", choices=["all", "solve", "batch16", "serving", "level"])
     # the level leg: single-level solves for a profiler (engine and strip height as given)
     ap.add_argument("--engine", default="stream", choices=["stream", "persistent", "fused"])
+    ap.add_argument("--method", default="padmm", choices=["padmm", "pdr", "alg1"])
     # strip height of the batch16 leg (-1: autotuned; a fixed height makes the launch sequence
     # independent of timing, e.g. under a profiler)
     ap.add_argument("--rows-per-warp", type=int, default=-1, choices=[-1, 0, 1, 2, 8, 32])

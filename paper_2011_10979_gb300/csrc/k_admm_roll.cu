@@ -8,18 +8,19 @@ int admm_fused_strip_w() { return roll::SW; }
 int admm_fused_warps() { return roll::WARPS; }
 
 int admm_fused_rows_per_warp(long strip_rows, bool storage16) {
-    // rows per warp: 8 (halo (8+3)/8) where that still gives about eight warps per SM; on smaller
+    // rows per warp: 8 (halo (8+3)/8) where that still gives at least ten warps per SM; on smaller
     // levels a warp's TY + 3 row steps are the latency of the whole iteration, so there strips of
-    // two or one row trade redundant halo work for a short chain.  With 16-bit storage, launches of
-    // at least 16 warps per SM even at 32 rows (batches, very large images) take 32 (halo
-    // (32+3)/32, the register-capped kernel).  Measured per iteration (FP32, single pairs): 320x240
-    // 4.1 us at 2 rows; 640x480 8.4-8.6 at 2 or 8; 1280x960 24.3 at 8 vs 31.6 at 32; 3840x2160
-    // 143 vs 149; a 64-pair batch 288 vs 304 in FP32 but 331 vs 285 with BF16 duals.
+    // two rows (at least eight warps per SM) or one row trade redundant halo work for a short
+    // chain.  With 16-bit storage, launches of at least 16 warps per SM even at 32 rows (batches,
+    // very large images) take 32 (halo (32+3)/32, the register-capped kernel).  Measured per
+    // iteration (FP32, single pairs): 320x240 4.0 us at 2 rows; 640x480 (9 warps per SM at 8 rows)
+    // 7.98 at 2 against 8.27 at 8; 1024x436 (13 per SM) 10.7 at 2 against 9.7 at 8; 1280x960 24.3
+    // at 8 vs 31.6 at 32; 3840x2160 143 vs 149; a 64-pair batch 288 vs 304 in FP32 but 331 vs 285
+    // with BF16 duals.
     const long sms = 152;
     if (storage16 && strip_rows / 32 >= 16L * sms) return 32;
-    const int cand[3] = {8, 2, 1};
-    for (int t : cand)
-        if (strip_rows / t >= 8L * sms) return t;
+    if (strip_rows / 8 >= 10L * sms) return 8;
+    if (strip_rows / 2 >= 8L * sms) return 2;
     return 1;
 }
 

@@ -864,7 +864,8 @@ bool admm_resident_fits(Geom g, int method) {
 int admm_resident_nc(Geom, int) { return admm_resident_cluster(); }
 
 // pDR's per-kernel engine takes 2n + 1 launches per iteration, so its resident form wins at every
-// size that fits; the ADMM methods and ALG1 (one launch per iteration) only up to RESIDENT_MAX_PX.
+// size that fits (with one sweep the runtime compares against the one-launch tile kernel
+// instead); the ADMM methods and ALG1 (one launch per iteration) only up to RESIDENT_MAX_PX.
 bool admm_resident_preferred(Geom g, int method) { return method == 2 || (long)g.H * g.W <= RESIDENT_MAX_PX; }
 
 cudaError_t launch_admm_resident(const ResArgs &a, int nclusters, int nc, size_t smem, int prec, int prec_flow,
