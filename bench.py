@@ -572,9 +572,10 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streaming pADMM kernel on the
-# 640 x 480 level (ncu, cold cache), for the strip height the built-in rule takes there.  Set to
-# None whenever that kernel changes, until it is captured again.
-ROLL_640_DRAM_BYTES = None
+# 640 x 480 level (ncu, cold cache), for the strip height the built-in rule takes there (2 rows):
+# 16.04 MB read, 0 written (the written planes stay in L2).  Set to None whenever that kernel
+# changes, until it is captured again.
+ROLL_640_DRAM_BYTES = 16.04e6
 
 
 def kernel_roofline(flow, torch, dev, pr, reps=20):
