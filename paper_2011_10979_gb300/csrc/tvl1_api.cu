@@ -282,6 +282,20 @@ bool pdr_tile_of(const of_params *p) {
 // 2.7 / 4.3 at 80x60, 4.3 / 4.3 at 120x90, 6.0 / 4.4 at 160x120).
 constexpr long PDR_TILE_RESIDENT_MAX_PX = 12000;
 
+// Whether a single pair's streamed ADMM level runs two iterations per launch (k_admm_tile.cu): a
+// fixed schedule (the stopping test needs the state after every tenth iteration in a known buffer),
+// the built-in strip rule (a pinned or autotuned height asks for the row-streaming kernel), and a
+// level whose state stays in L2.  Measured per iteration against the row-streaming kernel: 320x240
+// 3.21 against 3.99 us, 640x480 7.86 against 7.98; but 1920x1080 52.0 against 39.6 (DRAM-bound
+// there, where the tiles' 34% larger staged frame costs more than the saved launch).
+constexpr long TILE2_MAX_PX = 320000;
+
+bool admm_tile2_of(const of_params *p, bool batched, Geom g) {
+    return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->tol == 0.0 &&
+           p->rows_per_warp == 0 && (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM) &&
+           (long)g.H * g.W <= TILE2_MAX_PX;
+}
+
 bool use_resident(const of_params *p, Geom g) {
     if (!admm_resident_fits(g, p->method)) return false;
     if (p->engine == OF_ENGINE_RESIDENT) return true;
@@ -862,9 +876,13 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
             // the non-resident pairs (ALG1)
             const bool streamed = !persl && (batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1);
-            for (int it = 0; streamed && it < rest; ++it) {
+            // single pair, ADMM, fixed schedule, the built-in strip rule: two iterations per launch
+            const bool tile2 = streamed && admm_tile2_of(p, batched, geom_of(*pc[0].pl, l));
+            int par = start2, last_nb = 0;  // the two-iteration path's buffer parity and last block count
+            for (int it = 0, step = 1; streamed && it < rest; it += step) {
+                step = tile2 && it + 1 < rest ? 2 : 1;
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
-                const bool final_it = last_warp && it == rest - 1;
+                const bool final_it = last_warp && it + step == rest;
                 IterArgs a{};
                 a.k = k;
                 if (!batched) {
@@ -873,8 +891,9 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     const Fields *bf = bufs_of(c);
                     const void *const *dat = data_of(c);
                     a.g = g;
-                    a.in = bf[pingpong ? (start2 + it) & 1 : start2];
-                    a.out = bf[pingpong ? (start2 + it + 1) & 1 : start2];
+                    a.in = bf[tile2 ? par : pingpong ? (start2 + it) & 1 : start2];
+                    a.out = bf[tile2 ? par ^ 1 : pingpong ? (start2 + it + 1) & 1 : start2];
+                    par ^= 1;
                     a.Ix = dat[0];
                     a.Iy = dat[1];
                     a.It = dat[2];
@@ -889,9 +908,13 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         else launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
                         launch_cp(a, prec, pflow, s);
+                    } else if (step == 2) {
+                        launch_admm_tile2(a, prec, pflow, s);
+                        last_nb = admm_tile2_blocks(g);
                     } else {
                         if (plain) launch_admm_plain(a, s);
                         else launch_admm_fused(a, prec, pflow, s);
+                        last_nb = blocks_of(g, l);
                     }
                     if (check) {
                         const int nb = blocks_of(g, l);
@@ -938,7 +961,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 else launch_count_iters(&m->iters, nullptr, rest, s);
             }
             if (pingpong) {
-                const int fin = (start + p->iters) & 1;
+                const int fin = tile2 ? par : (start + p->iters) & 1;
                 if (p->tol > 0.0 && (rest & 1))
                     for (int q = 0; q < n; ++q)
                         if (!(res1 || (batched && B.res[l][q])))  // the resident engine writes buf[fin] itself
@@ -957,7 +980,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     launch_reduce_check_batched(bpart, ps, n, 0.0, 0, 1, s);
                 } else {
                     const Geom g = geom_of(*pc[0].pl, l);
-                    launch_sum(pc[0].partials, blocks_of(g, l), &pc[0].misc->res_final, s);
+                    launch_sum(pc[0].partials, tile2 ? last_nb : blocks_of(g, l), &pc[0].misc->res_final, s);
                 }
             }
         }
