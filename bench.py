@@ -189,7 +189,8 @@ def run_batch16(args):
 def run_level(args):
     """Single-level solves for a profiler: the 40x30 and 640x480 levels of the bench pair's kind
     (one warp, 30 inner iterations, three solves each) of --method (pADMM unless set) on the given
-    engine, strip height --rows-per-warp (8 unless set; ADMM only).  A 40x30 level runs a handful of
+    engine, strip height --rows-per-warp (ADMM only; unset: the built-in rule, which on the
+    streaming engine runs these levels two iterations per launch).  A 40x30 level runs a handful of
     warps, each walking its strip alone on its SM, so it shows the latency of one warp's row steps;
     with --method pdr the 640x480 level runs the one-launch pDR tile kernel."""
     import torch
@@ -200,7 +201,7 @@ def run_level(args):
     build()
     ctx = flow.Context(0)
     eng = {"stream": flow.OF_ENGINE_STREAM, "persistent": flow.OF_ENGINE_PERSISTENT, "fused": flow.OF_ENGINE_FUSED}
-    ty = args.rows_per_warp if args.rows_per_warp > 0 else 8
+    ty = args.rows_per_warp if args.rows_per_warp > 0 else 0
     for (h, w) in ((30, 40), (480, 640)):
         pr = synth.affine_rect_pair(h, w) if h >= 120 else synth.random_affine_rect_pair(h, w, 3)
         I0, I1 = torch.from_numpy(pr.I0).to(dev), torch.from_numpy(pr.I1).to(dev)
@@ -571,19 +572,19 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
                                  "ms_per_solve": {"%dx%d" % (w, h): round(v, 3) for (h, w), v in single_ms.items()}}}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streaming pADMM kernel on the
-# 640 x 480 level (ncu, cold cache), for the strip height the built-in rule takes there (2 rows):
-# 16.04 MB read, 0 written (the written planes stay in L2).  Set to None whenever that kernel
-# changes, until it is captured again.
-ROLL_640_DRAM_BYTES = 16.04e6
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the pADMM kernel that runs the
+# 640 x 480 level of the bench solve (ncu, cold cache): k_admm_tile2, two iterations per launch.
+# Set to None whenever that kernel changes, until it is captured again.
+TILE2_640_DRAM_BYTES = None
 
 
 def kernel_roofline(flow, torch, dev, pr, reps=20):
-    """Per-launch time of the streaming pADMM iteration kernel on the 640 x 480 level where it runs:
-    inside the solve's CUDA graph.  Two graph-launched single-level solves of the bench pair, with
-    220 and 20 inner iterations, are timed with CUDA events on their stream; the difference / 200
-    is one iteration (one kernel launch and its share of graph launch gaps).  Algorithmic traffic:
-    13 planes read + 10 written, FP32 = 92 B per pixel-iteration."""
+    """Per-launch time of the pADMM kernel on the 640 x 480 level where it runs: inside the solve's
+    CUDA graph.  With the bench's fixed schedule that level runs two inner iterations per launch
+    (k_admm_tile2).  Two graph-launched single-level solves of the bench pair, with 220 and 20 inner
+    iterations, are timed with CUDA events on their stream; the difference / 100 is one launch (two
+    iterations and its share of graph launch gaps).  Algorithmic traffic: 13 planes read + 10
+    written, FP32 = 92 B per pixel-iteration, 184 B per pixel and launch."""
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -609,19 +610,19 @@ def kernel_roofline(flow, torch, dev, pr, reps=20):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t[iters] = e0.elapsed_time(e1) / reps / 1e3
-    ty = flow.of_rows_per_warp(ctx, [(H, W)], flow.default_params(lam=LAM, beta=BETA, levels=1,
-                                                                    engine=flow.OF_ENGINE_STREAM))[0]
     ctx.close()
-    per = (t[220] - t[20]) / 200.0
-    bytes_per_launch = 92.0 * H * W
+    per = (t[220] - t[20]) / 100.0         # one launch = two iterations
+    bytes_per_launch = 2 * 92.0 * H * W
     achieved = bytes_per_launch / per / 1e9
     # the level's working set stays in L2: its bandwidth for a working set of the same size
     # (half read, half written, streamed 400 times in one launch)
-    l2 = flow.of_l2_bandwidth(int(bytes_per_launch), 400)
-    return {"kernel": "k_admm_roll<float,float,1,0,%d> (640x480 level)" % ty, "bound": "hbm", "achieved": achieved,
+    l2 = flow.of_l2_bandwidth(int(bytes_per_launch / 2), 400)
+    return {"kernel": "k_admm_tile2<float,float,1,0,32> (640x480 level, two iterations per launch)",
+            "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
-            "traffic": ROLL_640_DRAM_BYTES, "us_per_launch": per * 1e6, "algorithmic_bytes_per_launch": bytes_per_launch,
-            "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 200",
+            "traffic": TILE2_640_DRAM_BYTES, "us_per_launch": per * 1e6,
+            "us_per_iteration": per * 1e6 / 2, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 100 launches",
             "l2_peak": l2, "frac_of_l2": achieved / l2,
             "note": "the 640x480 level's 28 MB state stays in the 129 MB L2 between iterations; l2_peak is the "
                     "library's L2 streaming probe over a 28 MB read+write working set"}
