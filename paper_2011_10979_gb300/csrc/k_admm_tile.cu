@@ -30,21 +30,22 @@ namespace tvl1 {
 namespace {
 
 enum { SY0 = 0, SS = 6, SW_ = 7, SU = 8, SV = 9, SIX = 10, SIY = 11, SIT = 12, SDP = 13, NPL = 16 };
-template <int TT> struct Shape {
-    static constexpr int FS = TT + 5, FN = FS * FS, NT = TT == 32 ? 512 : 256, SMEM = NPL * FN * 4;
+// NI iterations per launch on TT x TT tiles: the frame spans offsets -NI - 1 .. TT + NI - 1.
+template <int TT, int NI> struct Shape {
+    static constexpr int FS = TT + 2 * NI + 1, FN = FS * FS, NT = TT == 32 ? 512 : 256, SMEM = NPL * FN * 4;
 };
 
 template <int N> using IC = std::integral_constant<int, N>;
 
-template <typename T, typename TF, bool HAS_W, int VARIANT, int TT>
-__global__ void __launch_bounds__(Shape<TT>::NT) k_admm_tile2(IterArgs A) {
-    constexpr int FS = Shape<TT>::FS, FN = Shape<TT>::FN, NT = Shape<TT>::NT;
+template <typename T, typename TF, bool HAS_W, int VARIANT, int TT, int NI>
+__global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
+    constexpr int FS = Shape<TT, NI>::FS, FN = Shape<TT, NI>::FN, NT = Shape<TT, NI>::NT, OFF = NI + 1;
     extern __shared__ float sm[];
     __shared__ double red[32];
     const int H = A.g.H, W = A.g.W, P = A.g.pitch;
     if (A.done && *A.done) return;
     const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
-    const int fi = i0 - 3, fj = j0 - 3;  // global coordinates of frame cell (0, 0)
+    const int fi = i0 - OFF, fj = j0 - OFF;  // global coordinates of frame cell (0, 0)
     auto S = [&](int k) { return sm + k * FN; };
     const int YF[6] = {F_P1, F_P2, F_Q11, F_Q12, F_Q21, F_Q22};
     // ---- stage the frame; all of a thread's loads are issued before its shared-memory stores
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(Shape<TT>::NT) k_admm_tile2(IterArgs A) {
             const int i = fi + li, j = fj + lj;
             const bool ok = x < FN && i >= 0 && i < H && j >= 0 && j < W;
             const bool ok2 = ok && li >= 1 && lj >= 1;
-            const bool ok3 = ok2 && li >= 2 && lj >= 2 && li <= TT + 3 && lj <= TT + 3;
+            const bool ok3 = ok2 && li >= 2 && lj >= 2 && li <= FS - 2 && lj <= FS - 2;
             const size_t o = ok ? (size_t)i * P + j : 0;
 #pragma unroll
             for (int k = 0; k < 6; ++k) v[r][k] = ((HAS_W || k >= 2) && ok) ? ldT<T>(A.in.f[YF[k]], o) : 0.f;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(Shape<TT>::NT) k_admm_tile2(IterArgs A) {
     auto for_cells = [&](auto LO_, auto HI_, auto &&f) {
         constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1;
         for (int t = threadIdx.x; t < n * n; t += NT) {
-            const int li = lo + 3 + t / n, lj = lo + 3 + t % n;
+            const int li = lo + OFF + t / n, lj = lo + OFF + t % n;
             const int i = fi + li, j = fj + lj;
             if (i >= 0 && i < H && j >= 0 && j < W) f(li * FS + lj, i, j);
         }
@@ -153,24 +154,31 @@ __global__ void __launch_bounds__(Shape<TT>::NT) k_admm_tile2(IterArgs A) {
         dq2n = div2(ex ? S(SY0 + 4)[x] : 0.f, wx ? S(SY0 + 4)[x - 1] : 0.f, hy ? S(SY0 + 5)[x] : 0.f,
                     nyy ? S(SY0 + 5)[x - FS] : 0.f);
     };
-    // ---- iteration k
-    div_phase(IC<-2>{}, IC<TT + 1>{});
-    __syncthreads();
-    y_phase(IC<-2>{}, IC<TT>{});
-    __syncthreads();
-    // s^{k+1} and Lambda^{k+1} on -1 .. TT, rounded as stored (only the pixel itself reads them here)
-    for_cells(IC<-1>{}, IC<TT>{}, [&](int x, int i, int j) {
-        float dpn, dq1n, dq2n, s_new;
-        div_new(x, i, j, dpn, dq1n, dq2n);
-        float w = S(SW_)[x], u = S(SU)[x], v = S(SV)[x];
-        finish_pixel<HAS_W, VARIANT>(S(SIX)[x], S(SIY)[x], S(SIT)[x], S(SS)[x], w, u, v, dpn, dq1n, dq2n, K, s_new);
-        S(SS)[x] = storage_round<T>(s_new);
-        if (HAS_W) S(SW_)[x] = storage_round<TF>(w);
-        S(SU)[x] = storage_round<TF>(u);
-        S(SV)[x] = storage_round<TF>(v);
-    });
-    __syncthreads();
-    // ---- iteration k + 1
+    // ---- iterations k .. k + NI - 2: an iteration E pixels from the last one computes div y on
+    // -1 - E .. TT + E, y on -1 - E .. TT - 1 + E, and s, Lambda (rounded as stored; only the pixel
+    // itself reads them in that phase) on -E .. TT - 1 + E
+    auto iteration = [&](auto E_) {
+        constexpr int e = decltype(E_)::value;
+        div_phase(IC<-1 - e>{}, IC<TT + e>{});
+        __syncthreads();
+        y_phase(IC<-1 - e>{}, IC<TT - 1 + e>{});
+        __syncthreads();
+        for_cells(IC<-e>{}, IC<TT - 1 + e>{}, [&](int x, int i, int j) {
+            float dpn, dq1n, dq2n, s_new;
+            div_new(x, i, j, dpn, dq1n, dq2n);
+            float w = S(SW_)[x], u = S(SU)[x], v = S(SV)[x];
+            finish_pixel<HAS_W, VARIANT>(S(SIX)[x], S(SIY)[x], S(SIT)[x], S(SS)[x], w, u, v, dpn, dq1n, dq2n, K,
+                                         s_new);
+            S(SS)[x] = storage_round<T>(s_new);
+            if (HAS_W) S(SW_)[x] = storage_round<TF>(w);
+            S(SU)[x] = storage_round<TF>(u);
+            S(SV)[x] = storage_round<TF>(v);
+        });
+        __syncthreads();
+    };
+    if constexpr (NI >= 3) iteration(IC<2>{});
+    iteration(IC<1>{});
+    // ---- the last iteration: its finish on the tile stores the state
     div_phase(IC<-1>{}, IC<TT>{});
     __syncthreads();
     y_phase(IC<-1>{}, IC<TT - 1>{});
@@ -202,30 +210,37 @@ __global__ void __launch_bounds__(Shape<TT>::NT) k_admm_tile2(IterArgs A) {
     }
 }
 
-template <typename T, typename TF, bool HAS_W, int VARIANT, int TT> void launch_tt(const IterArgs &a, cudaStream_t s) {
-    using SH = Shape<TT>;
+template <typename T, typename TF, bool HAS_W, int VARIANT, int TT, int NI>
+void launch_tt(const IterArgs &a, cudaStream_t s) {
+    using SH = Shape<TT, NI>;
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_admm_tile2<T, TF, HAS_W, VARIANT, TT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_admm_tile2<T, TF, HAS_W, VARIANT, TT, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SH::SMEM);
     });
     dim3 grid((a.g.W + TT - 1) / TT, (a.g.H + TT - 1) / TT);
-    k_admm_tile2<T, TF, HAS_W, VARIANT, TT><<<grid, SH::NT, SH::SMEM, s>>>(a);
+    k_admm_tile2<T, TF, HAS_W, VARIANT, TT, NI><<<grid, SH::NT, SH::SMEM, s>>>(a);
 }
 
-template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_v(const IterArgs &a, cudaStream_t s) {
-    if (admm_tile2_size(a.g) == 16) launch_tt<T, TF, HAS_W, VARIANT, 16>(a, s);
-    else launch_tt<T, TF, HAS_W, VARIANT, 32>(a, s);
+template <typename T, typename TF, bool HAS_W, int VARIANT> void launch_v(const IterArgs &a, int ni, cudaStream_t s) {
+    const bool small = admm_tile2_size(a.g) == 16;
+    if (ni == 3) {
+        if (small) launch_tt<T, TF, HAS_W, VARIANT, 16, 3>(a, s);
+        else launch_tt<T, TF, HAS_W, VARIANT, 32, 3>(a, s);
+    } else {
+        if (small) launch_tt<T, TF, HAS_W, VARIANT, 16, 2>(a, s);
+        else launch_tt<T, TF, HAS_W, VARIANT, 32, 2>(a, s);
+    }
 }
 
-template <typename T, typename TF> void launch_m(const IterArgs &a, cudaStream_t s) {
+template <typename T, typename TF> void launch_m(const IterArgs &a, int ni, cudaStream_t s) {
     const bool has_w = a.k.beta != 0.f;
     const int variant = (a.k.method == 1 ? 1 : 0) | (a.k.a_tilde_mode == 1 ? 2 : 0);
     switch (variant) {
-    case 0: return has_w ? launch_v<T, TF, true, 0>(a, s) : launch_v<T, TF, false, 0>(a, s);
-    case 1: return has_w ? launch_v<T, TF, true, 1>(a, s) : launch_v<T, TF, false, 1>(a, s);
-    case 2: return has_w ? launch_v<T, TF, true, 2>(a, s) : launch_v<T, TF, false, 2>(a, s);
-    default: return has_w ? launch_v<T, TF, true, 3>(a, s) : launch_v<T, TF, false, 3>(a, s);
+    case 0: return has_w ? launch_v<T, TF, true, 0>(a, ni, s) : launch_v<T, TF, false, 0>(a, ni, s);
+    case 1: return has_w ? launch_v<T, TF, true, 1>(a, ni, s) : launch_v<T, TF, false, 1>(a, ni, s);
+    case 2: return has_w ? launch_v<T, TF, true, 2>(a, ni, s) : launch_v<T, TF, false, 2>(a, ni, s);
+    default: return has_w ? launch_v<T, TF, true, 3>(a, ni, s) : launch_v<T, TF, false, 3>(a, ni, s);
     }
 }
 
@@ -239,12 +254,12 @@ int admm_tile2_blocks(Geom g) {
     return ((g.W + tt - 1) / tt) * ((g.H + tt - 1) / tt);
 }
 
-void launch_admm_tile2(const IterArgs &a, int prec, int prec_flow, cudaStream_t s) {
-    if (prec == PREC_F32) launch_m<float, float>(a, s);
-    else if (prec == PREC_F16 && prec_flow == PREC_F32) launch_m<__half, float>(a, s);
-    else if (prec == PREC_F16) launch_m<__half, __half>(a, s);
-    else if (prec_flow == PREC_F32) launch_m<__nv_bfloat16, float>(a, s);
-    else launch_m<__nv_bfloat16, __nv_bfloat16>(a, s);
+void launch_admm_tile2(const IterArgs &a, int ni, int prec, int prec_flow, cudaStream_t s) {
+    if (prec == PREC_F32) launch_m<float, float>(a, ni, s);
+    else if (prec == PREC_F16 && prec_flow == PREC_F32) launch_m<__half, float>(a, ni, s);
+    else if (prec == PREC_F16) launch_m<__half, __half>(a, ni, s);
+    else if (prec_flow == PREC_F32) launch_m<__nv_bfloat16, float>(a, ni, s);
+    else launch_m<__nv_bfloat16, __nv_bfloat16>(a, ni, s);
 }
 
 }  // namespace tvl1

@@ -289,6 +289,7 @@ constexpr long PDR_TILE_RESIDENT_MAX_PX = 12000;
 // 3.21 against 3.99 us, 640x480 7.86 against 7.98; but 1920x1080 52.0 against 39.6 (DRAM-bound
 // there, where the tiles' 34% larger staged frame costs more than the saved launch).
 constexpr long TILE2_MAX_PX = 320000;
+constexpr int TILE_ITERS = 3;  // iterations per launch (the last launch of a warp may run 2, or 1)
 
 bool admm_tile2_of(const of_params *p, bool batched, Geom g) {
     return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->tol == 0.0 &&
@@ -880,7 +881,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             const bool tile2 = streamed && admm_tile2_of(p, batched, geom_of(*pc[0].pl, l));
             int par = start2, last_nb = 0;  // the two-iteration path's buffer parity and last block count
             for (int it = 0, step = 1; streamed && it < rest; it += step) {
-                step = tile2 && it + 1 < rest ? 2 : 1;
+                step = tile2 ? std::min(TILE_ITERS, rest - it) : 1;
                 const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
                 const bool final_it = last_warp && it + step == rest;
                 IterArgs a{};
@@ -908,8 +909,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         else launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
                         launch_cp(a, prec, pflow, s);
-                    } else if (step == 2) {
-                        launch_admm_tile2(a, prec, pflow, s);
+                    } else if (step > 1) {
+                        launch_admm_tile2(a, step, prec, pflow, s);
                         last_nb = admm_tile2_blocks(g);
                     } else {
                         if (plain) launch_admm_plain(a, s);

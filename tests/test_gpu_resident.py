@@ -110,21 +110,21 @@ def test_mixed_batch_equals_single(ctx, prec, tol, engine, name):
 
 def test_resident_kernel_count(ctx):
     """A resident level launches one kernel per warp; the streaming engine one per inner iteration
-    (with a pinned strip height; by the built-in rule and a fixed schedule one per two iterations),
-    an iteration count per warp and the final residual sum."""
+    (with a pinned strip height; by the built-in rule and a fixed schedule one per three
+    iterations), an iteration count per warp and the final residual sum."""
     P = flow.default_params(lam=2.0, levels=1, warps=3, iters=100, engine=RESIDENT)
     n_res = flow.of_solve_kernel_count(ctx, 48, 64, P)
     P.engine = STREAM
     P.rows_per_warp = 2
     n_str = flow.of_solve_kernel_count(ctx, 48, 64, P)
     assert n_str - n_res == 3 * (100 + 1 - 1) + 1
-    P.rows_per_warp = 0
-    assert flow.of_solve_kernel_count(ctx, 48, 64, P) - n_res == 3 * (50 + 1 - 1) + 1
-    P.iters = 101  # an odd count ends each warp with one single-iteration launch
+    P.rows_per_warp = 0   # 33 launches of three iterations and one single-iteration launch per warp
+    assert flow.of_solve_kernel_count(ctx, 48, 64, P) - n_res == 3 * (34 + 1 - 1) + 1
+    P.iters = 101  # 33 launches of three and one of two
     P.engine = RESIDENT
     n_res = flow.of_solve_kernel_count(ctx, 48, 64, P)
     P.engine = STREAM
-    assert flow.of_solve_kernel_count(ctx, 48, 64, P) - n_res == 3 * (51 + 1 - 1) + 1
+    assert flow.of_solve_kernel_count(ctx, 48, 64, P) - n_res == 3 * (34 + 1 - 1) + 1
 
 
 def test_large_batch_streams_small_levels(ctx):

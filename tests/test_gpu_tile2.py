@@ -1,8 +1,9 @@
-"""Two ADMM inner iterations per launch (k_admm_tile2, single pairs with a fixed schedule and the
-built-in strip rule) against one launch per iteration of the row-streaming kernel (a pinned strip
-height) and the persistent engine: the state between the two iterations is rounded where the
-streaming kernel's stores round it, so the flows are bitwise equal, on tiles with ragged edges,
-both tile sizes, every ADMM variant, 16-bit storage and odd iteration counts."""
+"""Several ADMM inner iterations per launch (k_admm_tile2: three, the last launch of a warp two or
+one; single pairs with a fixed schedule and the built-in strip rule) against one launch per
+iteration of the row-streaming kernel (a pinned strip height) and the persistent engine: the state
+between the iterations is rounded where the streaming kernel's stores round it, so the flows are
+bitwise equal, on tiles with ragged edges, both tile sizes, every ADMM variant, 16-bit storage and
+iteration counts that end a warp with launches of one, two and three iterations."""
 import numpy as np
 import pytest
 
@@ -43,7 +44,7 @@ def _solve(ctx, pr, **kw):
 
 @pytest.mark.parametrize("H,W", [(1, 1), (3, 200), (200, 3), (37, 53), (203, 333), (480, 640), (436, 1024)])
 @pytest.mark.parametrize("name", list(VARIANTS))
-@pytest.mark.parametrize("iters", [22, 23])
+@pytest.mark.parametrize("iters", [22, 23, 24])
 def test_two_iterations_per_launch_equal_two_launches(ctx, H, W, name, iters):
     pr = _pair(H, W, 5 + H)
     kw = dict(lam=2.0, levels=1, warps=2, iters=iters, engine=flow.OF_ENGINE_STREAM, **VARIANTS[name])
