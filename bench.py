@@ -573,19 +573,19 @@ def serving_measure(flow, torch, dev, rate_hz=50.0, duration_s=15.0, drain_s=5.0
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the pADMM kernel that runs the
-# 640 x 480 level of the bench solve (ncu, cold cache): k_admm_tile2, two iterations per launch,
-# 16.00 MB read (the 13 input planes once), 0 written (the written planes stay in L2).  Set to None
-# whenever that kernel changes, until it is captured again.
-TILE2_640_DRAM_BYTES = 16.00e6
+# 640 x 480 level of the bench solve (ncu, cold cache): k_admm_tile2, three iterations per launch.
+# Set to None whenever that kernel changes, until it is captured again.
+TILE2_640_DRAM_BYTES = None
+ITERS_PER_LAUNCH = 3
 
 
 def kernel_roofline(flow, torch, dev, pr, reps=20):
     """Per-launch time of the pADMM kernel on the 640 x 480 level where it runs: inside the solve's
-    CUDA graph.  With the bench's fixed schedule that level runs two inner iterations per launch
+    CUDA graph.  With the bench's fixed schedule that level runs three inner iterations per launch
     (k_admm_tile2).  Two graph-launched single-level solves of the bench pair, with 220 and 20 inner
-    iterations, are timed with CUDA events on their stream; the difference / 100 is one launch (two
-    iterations and its share of graph launch gaps).  Algorithmic traffic: 13 planes read + 10
-    written, FP32 = 92 B per pixel-iteration, 184 B per pixel and launch."""
+    iterations, are timed with CUDA events on their stream; the difference / 200 is one iteration
+    (with its share of graph launch gaps), three of them one launch.  Algorithmic traffic: 13
+    planes read + 10 written, FP32 = 92 B per pixel-iteration, 276 B per pixel and launch."""
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -612,18 +612,18 @@ def kernel_roofline(flow, torch, dev, pr, reps=20):
         torch.cuda.synchronize(dev)
         t[iters] = e0.elapsed_time(e1) / reps / 1e3
     ctx.close()
-    per = (t[220] - t[20]) / 100.0         # one launch = two iterations
-    bytes_per_launch = 2 * 92.0 * H * W
+    per = (t[220] - t[20]) / 200.0 * ITERS_PER_LAUNCH   # one launch = three iterations
+    bytes_per_launch = ITERS_PER_LAUNCH * 92.0 * H * W
     achieved = bytes_per_launch / per / 1e9
     # the level's working set stays in L2: its bandwidth for a working set of the same size
     # (half read, half written, streamed 400 times in one launch)
-    l2 = flow.of_l2_bandwidth(int(bytes_per_launch / 2), 400)
-    return {"kernel": "k_admm_tile2<float,float,1,0,32> (640x480 level, two iterations per launch)",
+    l2 = flow.of_l2_bandwidth(int(bytes_per_launch / ITERS_PER_LAUNCH), 400)
+    return {"kernel": "k_admm_tile2<float,float,1,0,32> (640x480 level, three iterations per launch)",
             "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": src,
             "traffic": TILE2_640_DRAM_BYTES, "us_per_launch": per * 1e6,
-            "us_per_iteration": per * 1e6 / 2, "algorithmic_bytes_per_launch": bytes_per_launch,
-            "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 100 launches",
+            "us_per_iteration": per * 1e6 / ITERS_PER_LAUNCH, "algorithmic_bytes_per_launch": bytes_per_launch,
+            "timing": "graph-launched single-level solves, (t(220 iters) - t(20 iters)) / 200 x 3 per launch",
             "l2_peak": l2, "frac_of_l2": achieved / l2,
             "note": "the 640x480 level's 28 MB state stays in the 129 MB L2 between iterations; l2_peak is the "
                     "library's L2 streaming probe over a 28 MB read+write working set"}

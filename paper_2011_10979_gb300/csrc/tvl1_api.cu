@@ -289,7 +289,10 @@ constexpr long PDR_TILE_RESIDENT_MAX_PX = 12000;
 // 3.21 against 3.99 us, 640x480 7.86 against 7.98; but 1920x1080 52.0 against 39.6 (DRAM-bound
 // there, where the tiles' 34% larger staged frame costs more than the saved launch).
 constexpr long TILE2_MAX_PX = 320000;
-constexpr int TILE_ITERS = 3;  // iterations per launch (the last launch of a warp may run 2, or 1)
+// Iterations per launch (the last launch of a warp may run 2, or 1).  Measured per iteration at
+// 640x480 / 320x240: 7.86 / 3.21 us with 2, 7.36 / 3.04 with 3, 7.88 / 3.29 with 4 (a 41 x 41
+// frame: 64 registers and 108 KB of shared memory per block, and a third more halo work).
+constexpr int TILE_ITERS = 3;
 
 bool admm_tile2_of(const of_params *p, bool batched, Geom g) {
     return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->tol == 0.0 &&

@@ -44,8 +44,8 @@ def _solve(ctx, pr, **kw):
 
 @pytest.mark.parametrize("H,W", [(1, 1), (3, 200), (200, 3), (37, 53), (203, 333), (480, 640), (436, 1024)])
 @pytest.mark.parametrize("name", list(VARIANTS))
-@pytest.mark.parametrize("iters", [22, 23, 24])
-def test_two_iterations_per_launch_equal_two_launches(ctx, H, W, name, iters):
+@pytest.mark.parametrize("iters", [21, 22, 23, 24])
+def test_iterations_per_launch_equal_single_launches(ctx, H, W, name, iters):
     pr = _pair(H, W, 5 + H)
     kw = dict(lam=2.0, levels=1, warps=2, iters=iters, engine=flow.OF_ENGINE_STREAM, **VARIANTS[name])
     u0, v0, w0, s0 = _solve(ctx, pr, rows_per_warp=2, **kw)
@@ -57,7 +57,7 @@ def test_two_iterations_per_launch_equal_two_launches(ctx, H, W, name, iters):
 
 
 @pytest.mark.parametrize("prec,fp32_flow", [(1, 1), (2, 1), (2, 0), (1, 0)])
-def test_two_iterations_per_launch_on_16bit_storage(ctx, prec, fp32_flow):
+def test_iterations_per_launch_on_16bit_storage(ctx, prec, fp32_flow):
     pr = synth.affine_rect_pair(240, 320)
     kw = dict(lam=5.0, levels=2, warps=3, iters=30, precision=prec, fp32_flow=fp32_flow, engine=flow.OF_ENGINE_STREAM)
     a = _solve(ctx, pr, rows_per_warp=8, **kw)
@@ -66,7 +66,7 @@ def test_two_iterations_per_launch_on_16bit_storage(ctx, prec, fp32_flow):
 
 
 def test_whole_solve_against_the_persistent_engine(ctx):
-    """The bench workload's schedule shape (5 levels) on the 640x480 pair: the default engine (two
+    """The bench workload's schedule shape (5 levels) on the 640x480 pair: the default engine (three
     iterations per launch on its two streamed levels, resident below) against the persistent
     engine (every iteration of a warp in one launch, the row-streaming pipeline)."""
     pr = synth.affine_rect_pair()
@@ -78,8 +78,8 @@ def test_whole_solve_against_the_persistent_engine(ctx):
 
 def test_stopping_rule_and_pinned_heights_keep_one_launch_per_iteration(ctx):
     """tol > 0 (the test needs each tenth iteration's state) and a pinned height run the
-    row-streaming kernel; the flows still equal the two-iteration path's where the schedule runs
-    in full."""
+    row-streaming kernel; the flows still equal the tile path's where the schedule runs in
+    full."""
     P = flow.default_params(lam=5.0, levels=1, warps=1, iters=40, engine=flow.OF_ENGINE_STREAM)
     n_two = flow.of_solve_kernel_count(ctx, 480, 640, P)
     P.tol = 1e-30   # never met: the full schedule, one launch per iteration
