@@ -99,7 +99,7 @@ class Params:
     cp_tau: float = 0.1      # ALG1 dual step (Sec. 4)
     cp_sigma: float = 1.25   # ALG1 primal step 1 / (8 cp_tau) (Sec. 4, reading of the step rule)
     a_tilde_mode: int = 0    # 0: a~ = max M_s per warp (Prop. 3.1); 1: per-pixel a~_ij = M_s(ij)
-    c_adapt_iters: int = 0   # 0: fixed c; K: residual balancing of c in each level's first K iterations
+    c_adapt_iters: int = 0   # 0: fixed steps; K: balancing of c (pDR: sigma / tau) in each level's first K iterations
 
     def _c(self) -> _Params:
         return _Params(self.method, self.lam, self.beta, self.c, self.a, self.a_tilde, self.r,
@@ -143,6 +143,9 @@ def lib():
             "orc_adapt_residuals_flat": (d, [i, i, PP, PP, _D, _D, d, d, ctypes.POINTER(_Params), _D, _D]),
             "orc_inner_adapt_flat": (ctypes.c_longlong, [i, i, PP, _D, _D, _D, d, ctypes.POINTER(_Params), i, i,
                                                          _D, _D, _D]),
+            "orc_pdr_adapt_residuals_flat": (d, [i, i, PP, PP, d, d, ctypes.POINTER(_Params), _D, _D]),
+            "orc_inner_adapt_pdr_flat": (ctypes.c_longlong, [i, i, PP, _D, _D, _D, ctypes.POINTER(_Params), i, i,
+                                                             _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -356,6 +359,29 @@ def inner_adapt(state: State, Ix, Iy, It, a_tilde, params: Params, iters: int, w
     n = lib().orc_inner_adapt_flat(H, W, state._ptrs(), *[_p(x) for x in dat], a_tilde, ctypes.byref(P), iters,
                                    window, ctypes.byref(cc), ctypes.byref(mg), ctypes.byref(res))
     return int(n), res.value, cc.value, mg.value
+
+
+def pdr_adapt_residuals(prev: State, cur: State, sigma, tau, params: Params):
+    """pDR's balancing residuals of the step prev -> cur taken with (sigma, tau): the primal change
+    ||X^{k+1} - X^k|| / sigma and the dual change ||ybar^{k+1} - ybar^k|| / tau."""
+    H, W = prev["u"].shape
+    P = params._c()
+    rx, ry = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    lib().orc_pdr_adapt_residuals_flat(H, W, prev._ptrs(), cur._ptrs(), sigma, tau, ctypes.byref(P),
+                                       ctypes.byref(rx), ctypes.byref(ry))
+    return rx.value, ry.value
+
+
+def inner_adapt_pdr(state: State, Ix, Iy, It, params: Params, iters: int, window: int, theta: float = 1.0):
+    """A level's first warp of pDR under the adaptive steps; returns (iters_run, residual, theta,
+    margin)."""
+    dat = [_f64(x) for x in (Ix, Iy, It)]
+    H, W = dat[0].shape
+    P = params._c()
+    res, th, mg = ctypes.c_double(0.0), ctypes.c_double(theta), ctypes.c_double(float("inf"))
+    n = lib().orc_inner_adapt_pdr_flat(H, W, state._ptrs(), *[_p(x) for x in dat], ctypes.byref(P), iters, window,
+                                       ctypes.byref(th), ctypes.byref(mg), ctypes.byref(res))
+    return int(n), res.value, th.value, mg.value
 
 
 def energy(w, u, v, Ix, Iy, It, beta, lam):

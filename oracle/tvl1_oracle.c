@@ -312,8 +312,9 @@ typedef struct {
     double cp_tau;     /* ALG1 dual step */
     double cp_sigma;   /* ALG1 primal step */
     int a_tilde_mode;  /* 0: one a~ per warp (the paper's ||M_s||); 1: per-pixel a~_ij = M_s(ij) */
-    int c_adapt_iters; /* 0: fixed c; K > 0: residual balancing of c in the first K iterations of
-                          every level's first warp, c frozen afterwards (an extension) */
+    int c_adapt_iters; /* 0: fixed steps; K > 0: residual balancing in the first K iterations of
+                          every level's first warp, frozen afterwards (an extension): the ADMM
+                          step c, or pDR's sigma and tau with sigma tau fixed */
 } orc_params;
 
 typedef struct {
@@ -328,7 +329,7 @@ typedef struct {
 typedef struct {
     long long iters_run;
     double residual, energy, dual_value;
-    double c_final;      /* ADMM step c at the end of the solve */
+    double c_final;      /* ADMM step c (pDR: the primal step sigma) at the end of the solve */
     double adapt_margin; /* smallest |log| distance of a balancing test from its thresholds
                             (HUGE_VAL when no test ran): how far each decision was from a tie */
 } orc_stats;
@@ -728,6 +729,72 @@ long long orc_inner(int H, int W, orc_state *st, const double *Ix, const double 
     return k;
 }
 
+/* pDR (Sec. 3.1.2) leaves sigma and tau free.  The SRBGS preconditioner is built for
+ * T = I - sigma tau Laplace, so the balancing keeps sigma tau fixed and moves their ratio:
+ * sigma -> theta sigma, tau -> tau / theta.  Its residuals after the step prev -> cur are the
+ * primal change ||X^{k+1} - X^k|| / sigma and the dual change ||ybar^{k+1} - ybar^k|| / tau
+ * (each a change of its block's iterate per unit step); the rule of orc_adapt_rule then doubles
+ * theta when the primal change is more than 10 times the dual one and halves it in the opposite
+ * case.  Reading: a heuristic in the spirit of residual balancing for primal-dual methods; the
+ * paper gives no rule. */
+void orc_pdr_adapt_residuals(int H, int W, const orc_state *prev, const orc_state *cur, double sigma,
+                             double tau, const orc_params *P, double *rx, double *ry)
+{
+    size_t N = (size_t)H * (size_t)W;
+    int has_w = P->beta != 0.0;
+    const double *xp[3] = {prev->w, prev->u, prev->v}, *xc[3] = {cur->w, cur->u, cur->v};
+    const double *yp[6] = {prev->p1, prev->p2, prev->q11, prev->q12, prev->q21, prev->q22};
+    const double *yc[6] = {cur->p1, cur->p2, cur->q11, cur->q12, cur->q21, cur->q22};
+    double x2 = 0.0, y2 = 0.0;
+    for (int c = has_w ? 0 : 1; c < 3; ++c)
+        for (size_t k = 0; k < N; ++k) { double e = xc[c][k] - xp[c][k]; x2 += e * e; }
+    for (int c = has_w ? 0 : 2; c < 6; ++c)
+        for (size_t k = 0; k < N; ++k) { double e = yc[c][k] - yp[c][k]; y2 += e * e; }
+    *rx = sqrt(x2) / sigma;
+    *ry = sqrt(y2) / tau;
+}
+
+/* The first warp of a level under pDR's adaptive steps: like orc_inner_adapt, with theta (the
+ * factor on sigma, 1 / theta on tau) carried in *theta. */
+long long orc_inner_adapt_pdr(int H, int W, orc_state *st, const double *Ix, const double *Iy,
+                              const double *It, const orc_params *P, int iters, int window, double *theta,
+                              double *margin, double *res_out)
+{
+    size_t N = (size_t)H * (size_t)W;
+    double nrows = (double)N * (P->beta != 0.0 ? 3.0 : 2.0);
+    orc_params Q = *P;
+    orc_state prev;
+    memset(&prev, 0, sizeof(prev));
+    double **pk[9] = {&prev.w, &prev.u, &prev.v, &prev.p1, &prev.p2, &prev.q11, &prev.q12, &prev.q21, &prev.q22};
+    double *ps[9] = {st->w, st->u, st->v, st->p1, st->p2, st->q11, st->q12, st->q21, st->q22};
+    for (int f = 0; f < 9; ++f) *pk[f] = orc_alloc(N);
+    int kw = window < iters ? window : iters;
+    double res = 0.0;
+    for (int k = 0; k < kw; ++k) {
+        int test = (k + 1) % 10 == 0;
+        Q.sigma = P->sigma * *theta;
+        Q.tau = P->tau / *theta;
+        if (test)
+            for (int f = 0; f < 9; ++f) memcpy(*pk[f], ps[f], N * sizeof(double));
+        res = sqrt(orc_pdr_step(H, W, st, Ix, Iy, It, &Q) / nrows);
+        if (test) {
+            double rx, ry;
+            orc_pdr_adapt_residuals(H, W, &prev, st, Q.sigma, Q.tau, P, &rx, &ry);
+            double m1 = fabs(log(rx / (10.0 * ry))), m2 = fabs(log(ry / (10.0 * rx)));
+            if (m1 < *margin) *margin = m1;
+            if (m2 < *margin) *margin = m2;
+            *theta = orc_adapt_rule(*theta, rx, ry);
+        }
+    }
+    for (int f = 0; f < 9; ++f) free(*pk[f]);
+    Q.sigma = P->sigma * *theta;
+    Q.tau = P->tau / *theta;
+    long long n = kw;
+    if (iters > kw) n += orc_inner(H, W, st, Ix, Iy, It, 1.0, &Q, iters - kw, &res);
+    if (res_out) *res_out = res;
+    return n;
+}
+
 /* The first warp of a level under the adaptive step: the first `window` iterations run
  * without the stopping test and rebalance c after every 10th (residuals of that iteration,
  * with the c it used); the remaining iterations run with c frozen, their stopping test counted
@@ -783,7 +850,7 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
 {
     int L = P->levels;
     if (H < 1 || W < 1 || L < 1 || L > 32 || P->out_level < 0 || P->out_level >= L) return 1;
-    if (P->c_adapt_iters < 0 || P->c_adapt_iters % 10 != 0 || (P->c_adapt_iters > 0 && P->method >= 2)) return 2;
+    if (P->c_adapt_iters < 0 || P->c_adapt_iters % 10 != 0 || (P->c_adapt_iters > 0 && P->method == 3)) return 2;
     int Hs[32], Ws[32];
     double *P0[32], *P1[32];
     Hs[0] = H; Ws[0] = W;
@@ -806,7 +873,7 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
     double *u0 = orc_alloc(Nmax), *v0 = orc_alloc(Nmax);
     long long total = 0;
     double res = 0.0, a_tilde = 1.0;
-    double c_cur = P->c, margin = HUGE_VAL; /* the step carries from level to level */
+    double c_cur = P->c, theta = 1.0, margin = HUGE_VAL; /* the steps carry from level to level */
     orc_params Q = *P;
 
     for (int l = L - 1; l >= P->out_level; --l) {
@@ -833,11 +900,16 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
             memcpy(v0, st.v, n * sizeof(double));
             double msmax = orc_warp_linearise(h, w, P0[l], P1[l], I1x, I1y, u0, v0, P->beta, Ix, Iy, It);
             a_tilde = P->a_tilde > 0.0 ? P->a_tilde : (msmax > 1e-12 ? msmax : 1e-12);
-            if (P->c_adapt_iters > 0 && wp == 0) {
+            if (P->c_adapt_iters > 0 && wp == 0 && P->method == 2) {
+                total += orc_inner_adapt_pdr(h, w, &st, Ix, Iy, It, P, P->iters, P->c_adapt_iters, &theta, &margin,
+                                             &res);
+            } else if (P->c_adapt_iters > 0 && wp == 0) {
                 total += orc_inner_adapt(h, w, &st, Ix, Iy, It, a_tilde, P, P->iters, P->c_adapt_iters, &c_cur,
                                          &margin, &res);
             } else {
                 Q.c = c_cur;
+                Q.sigma = P->sigma * theta;
+                Q.tau = P->tau / theta;
                 total += orc_inner(h, w, &st, Ix, Iy, It, a_tilde, &Q, P->iters, &res);
             }
         }
@@ -850,7 +922,7 @@ int orc_solve(int H, int W, const double *I0, const double *I1, const orc_params
                 stats->residual = res;
                 stats->energy = orc_energy(h, w, st.w, st.u, st.v, Ix, Iy, It, P->beta, P->lambda);
                 stats->dual_value = P->method >= 2 ? NAN : orc_dual_value(n, It, st.s);
-                stats->c_final = c_cur;
+                stats->c_final = P->method == 2 ? P->sigma * theta : c_cur;
                 stats->adapt_margin = margin;
             }
         }
@@ -918,4 +990,23 @@ long long orc_inner_adapt_flat(int H, int W, double **fields, const double *Ix, 
     orc_state st;
     orc_state_from(&st, fields);
     return orc_inner_adapt(H, W, &st, Ix, Iy, It, a_tilde, P, iters, window, c, margin, res_out);
+}
+
+double orc_pdr_adapt_residuals_flat(int H, int W, double **prev_fields, double **cur_fields, double sigma,
+                                    double tau, const orc_params *P, double *rx, double *ry)
+{
+    orc_state prev, cur;
+    orc_state_from(&prev, prev_fields);
+    orc_state_from(&cur, cur_fields);
+    orc_pdr_adapt_residuals(H, W, &prev, &cur, sigma, tau, P, rx, ry);
+    return *rx;
+}
+
+long long orc_inner_adapt_pdr_flat(int H, int W, double **fields, const double *Ix, const double *Iy,
+                                   const double *It, const orc_params *P, int iters, int window, double *theta,
+                                   double *margin, double *res_out)
+{
+    orc_state st;
+    orc_state_from(&st, fields);
+    return orc_inner_adapt_pdr(H, W, &st, Ix, Iy, It, P, iters, window, theta, margin, res_out);
 }

@@ -1,6 +1,7 @@
 """Pins of the oracle's residual balancing of the ADMM step c (an extension: the paper fixes c;
 eq. (stepsize:constraint) of Sec. 3.1.1 bounds only a and a~, so any c > 0 keeps Prop. 3.1's
-metrics positive semidefinite).
+metrics positive semidefinite), and of pDR's sigma and tau (Sec. 3.1.2 leaves them free; the
+balancing keeps sigma tau and so the preconditioned system).
 
 * the balancing rule's two thresholds and its ties;
 * the residuals against the optimality conditions of the two subproblems of eq. (aug:pre1:vector),
@@ -236,8 +237,7 @@ def test_stopping_test_starts_after_the_window(orc):
 
 def test_bad_parameters_are_rejected(orc):
     I0, I1 = _pair()
-    for kw in (dict(c_adapt_iters=15), dict(c_adapt_iters=-10), dict(c_adapt_iters=20, method=2),
-               dict(c_adapt_iters=20, method=3)):
+    for kw in (dict(c_adapt_iters=15), dict(c_adapt_iters=-10), dict(c_adapt_iters=20, method=3)):
         with pytest.raises(ValueError):
             orc.solve(I0, I1, orc.Params(levels=1, warps=1, iters=5, **kw))
 
@@ -285,3 +285,120 @@ def test_balancing_rescues_a_bad_step(orc):
     n1, r1, c1, _ = orc.inner_adapt(orc.State.zeros(H, W), Ix, Iy, It, at, P, 20000, 100, P.c)
     assert n0 == 20000 and r0 > 1e-5
     assert n1 < 20000 and r1 < 1e-6 and c1 > 0.05
+
+
+# ------------------------------------------------------------------ pDR: sigma and tau with sigma tau fixed
+def test_pdr_balancing_keeps_the_preconditioned_system(orc):
+    """Scaling sigma by theta and tau by 1 / theta (theta a power of two) keeps sigma tau, hence
+    T = I - sigma tau Laplace and its SRBGS preconditioner: with ybar = 0 and Xbar = X the right-hand
+    side is X for every theta, so the X-update is bitwise the same; a step that scaled sigma alone
+    would differ."""
+    H, W = 7, 9
+    rng = np.random.default_rng(8)
+    Ix, Iy, It = (rng.normal(size=(H, W)) * s for s in (0.4, 0.4, 0.2))
+    base = orc.State.zeros(H, W)
+    for k in ("w", "u", "v"):
+        base[k] = rng.normal(size=(H, W))
+    for a, b in (("wb", "w"), ("ub", "u"), ("vb", "v")):
+        base[a] = base[b].copy()
+    out = {}
+    for th in (1.0, 4.0, 0.125):
+        st = base.copy()
+        orc.pdr_step(st, Ix, Iy, It, orc.Params(method=2, lam=0.3, sigma=2.0 * th, tau=0.4 / th))
+        out[th] = st
+    for th in (4.0, 0.125):
+        for k in ("w", "u", "v"):
+            assert np.array_equal(out[th][k], out[1.0][k]), (th, k)
+    st = base.copy()
+    orc.pdr_step(st, Ix, Iy, It, orc.Params(method=2, lam=0.3, sigma=8.0, tau=0.4))
+    assert not np.array_equal(st["u"], out[1.0]["u"])
+
+
+def test_pdr_residuals_are_the_per_step_changes(orc):
+    H, W = 5, 6
+    rng = np.random.default_rng(9)
+    a, b = orc.State.zeros(H, W), orc.State.zeros(H, W)
+    for st in (a, b):
+        for k in orc.STATE_FIELDS:
+            st[k] = rng.normal(size=(H, W))
+    for beta in (0.05, 0.0):
+        P = orc.Params(method=2, beta=beta)
+        rx, ry = orc.pdr_adapt_residuals(a, b, 2.0, 0.4, P)
+        xs = ("w", "u", "v") if beta else ("u", "v")
+        ys = ("p1", "p2", "q11", "q12", "q21", "q22") if beta else ("q11", "q12", "q21", "q22")
+        assert rx == pytest.approx(np.sqrt(sum(((b[k] - a[k]) ** 2).sum() for k in xs)) / 2.0, rel=1e-14)
+        assert ry == pytest.approx(np.sqrt(sum(((b[k] - a[k]) ** 2).sum() for k in ys)) / 0.4, rel=1e-14)
+
+
+def _pdr_adaptive_level(orc, st, I0, I1, P, theta, every_warp=False, period=10):
+    I1x, I1y = orc.derivatives(I1)
+    for wp in range(P.warps):
+        Ix, Iy, It, _ = orc.warp_linearise(I0, I1, I1x, I1y, st["u"].copy(), st["v"].copy(), P.beta)
+        K = P.c_adapt_iters if (wp == 0 or every_warp) else 0
+        for k in range(P.iters):
+            test = k < K and (k + 1) % period == 0
+            prev = st.copy() if test else None
+            Q = replace(P, sigma=P.sigma * theta, tau=P.tau / theta)
+            orc.pdr_step(st, Ix, Iy, It, Q)
+            if test:
+                rx, ry = orc.pdr_adapt_residuals(prev, st, Q.sigma, Q.tau, P)
+                theta = orc.adapt_rule(theta, rx, ry)
+    return theta
+
+
+def _pdr_adaptive_two_levels(orc, I0, I1, P, carry=True, every_warp=False, period=10):
+    H, W = I0.shape
+    Hc, Wc = orc.level_size(H, P.eta), orc.level_size(W, P.eta)
+    st = orc.State.zeros(Hc, Wc)
+    th = _pdr_adaptive_level(orc, st, orc.downsample(I0, Hc, Wc, P.eta), orc.downsample(I1, Hc, Wc, P.eta), P, 1.0,
+                             every_warp, period)
+    fine = orc.State.zeros(H, W)
+    fine["w"] = orc.upsample(st["w"], H, W, 1.0)
+    fine["u"] = orc.upsample(st["u"], H, W, W / Wc)
+    fine["v"] = orc.upsample(st["v"], H, W, H / Hc)
+    for a, b in (("wb", "w"), ("ub", "u"), ("vb", "v")):
+        fine[a] = fine[b].copy()
+    th = _pdr_adaptive_level(orc, fine, I0, I1, P, th if carry else 1.0, every_warp, period)
+    return fine["u"], fine["v"], th
+
+
+@pytest.mark.parametrize("kw,plants", [(dict(sigma=32.0, tau=0.025), True), (dict(sigma=64.0, tau=0.0125), True),
+                                       (dict(sigma=0.125, tau=6.4), False)])
+def test_pdr_window_schedule_is_the_composition_of_its_pinned_steps(orc, kw, plants):
+    """The ratio far too large (the planted mistakes each change the result) and far too small
+    (balanced within the first warp, so the window-in-every-warp plant would not show)."""
+    I0, I1 = _pair()
+    P = orc.Params(method=2, lam=5.0, levels=2, warps=2, iters=35, c_adapt_iters=20, **kw)
+    u, v, _, st = orc.solve(I0, I1, P)
+    cu_, cv_, th = _pdr_adaptive_two_levels(orc, I0, I1, P)
+    np.testing.assert_allclose(u, cu_, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(v, cv_, rtol=0, atol=1e-12)
+    assert st["c_final"] == P.sigma * th and th != 1.0
+    for plant in ((dict(carry=False), dict(every_warp=True), dict(period=5)) if plants else ()):
+        pu, pv, pth = _pdr_adaptive_two_levels(orc, I0, I1, P, **plant)
+        assert pth != th or max(np.abs(pu - u).max(), np.abs(pv - v).max()) > 1e-6, plant
+
+
+@pytest.mark.slow
+def test_pdr_frozen_steps_reach_the_certified_minimum(orc):
+    """With theta frozen after the window the iteration is Prop. 3.2's pDR with fixed steps: from a
+    sigma / tau ratio 256 times too large or too small it reaches the pADMM-certified minimum."""
+    H, W = 8, 8
+    rng = np.random.default_rng(21)
+    y_, x_ = np.mgrid[0:H, 0:W].astype(float)
+    img = np.sin(0.9 * x_ + 0.3) + np.cos(0.7 * y_ - 0.2 * x_)
+    d = dict(Ix=0.3 * np.cos(0.9 * x_ + 0.3), Iy=-0.2 * np.sin(0.7 * y_ - 0.2 * x_),
+             It=0.15 * img + 0.05 * rng.normal(size=(H, W)))
+    beta, lam = 0.05, 0.8
+    at = float((beta ** 2 + d["Ix"] ** 2 + d["Iy"] ** 2).max())
+    st = orc.State.zeros(H, W)
+    orc.inner(st, d["Ix"], d["Iy"], d["It"], at, orc.Params(method=0, lam=lam, beta=beta), 150000)
+    ref = orc.energy(st["w"], st["u"], st["v"], d["Ix"], d["Iy"], d["It"], beta, lam)
+    for th0 in (1 / 16.0, 16.0):
+        P = orc.Params(method=2, lam=lam, beta=beta, sigma=2.0 * th0, tau=0.4 / th0)
+        st = orc.State.zeros(H, W)
+        n, res, th, _ = orc.inner_adapt_pdr(st, d["Ix"], d["Iy"], d["It"], P, 100000, 100)
+        E = orc.energy(st["w"], st["u"], st["v"], d["Ix"], d["Iy"], d["It"], beta, lam)
+        assert th != 1.0 and 0.25 <= th0 * th <= 1.0, (th0, th)   # the ratio ends balanced
+        assert abs(E - ref) < 1e-5 * ref, (th0, E, ref)
+        assert res < 1e-8
