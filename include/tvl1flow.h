@@ -125,20 +125,24 @@ typedef struct {
                             decision taken on it) can differ in the last FP32 digits.  Used by
                             of_solve and of_solve_batch; the step-level entry points and the
                             serving loop use the built-in choice.                             */
-    int c_adapt_iters;   /* ADMM methods, opt-in (an extension, not in the paper): 0 = the fixed
-                            step c of Sec. 4.  K > 0 (a multiple of 10): in the first warp of
-                            every pyramid level, after each 10th of its first K inner
-                            iterations, c is rescaled by residual balancing: with r the
-                            constraint residual ||A s + B y|| and d the dual residual of the
-                            preconditioned ADMM, c(B^*A ds - (a I - B^*B) dy, (M_s - a~) ds)
-                            (ds, dy: the change of s and y over the iteration), c is doubled
-                            when r > 10 d and halved when d > 10 r.  After those K iterations c
-                            is frozen for the rest of the level (its fixed-metric convergence,
-                            Prop. 3.1, applies from there on); the next finer level starts its
-                            window from that value.  The stopping test (tol) starts after the
-                            window.  Single pairs (of_solve, of_solve_host, n = 1) on the fused
-                            engines only: OF_EINVAL for pDR, ALG1, the plain engine, batches,
-                            the serving loop and the step-level entry points.                  */
+    int c_adapt_iters;   /* ADMM methods and pDR, opt-in (an extension, not in the paper): 0 =
+                            the fixed steps of Sec. 4.  K > 0 (a multiple of 10): in the first
+                            warp of every pyramid level, after each 10th of its first K inner
+                            iterations, the steps are rebalanced.  ADMM: c, by residual balancing:
+                            with r the constraint residual ||A s + B y|| and d the dual residual
+                            of the preconditioned ADMM, c(B^*A ds - (a I - B^*B) dy,
+                            (M_s - a~) ds) (ds, dy: the change of s and y over the iteration), c
+                            is doubled when r > 10 d and halved when d > 10 r.  pDR (one
+                            Gauss-Seidel sweep): sigma -> theta sigma, tau -> tau / theta with
+                            sigma tau (so T and its preconditioner) unchanged; theta is doubled
+                            when ||X^{k+1} - X^k|| / sigma > 10 ||ybar^{k+1} - ybar^k|| / tau and
+                            halved in the opposite case.  After those K iterations the steps are
+                            frozen for the rest of the level (its fixed-step convergence, Props.
+                            3.1 and 3.2, applies from there on); the next finer level starts its
+                            window from them.  The stopping test (tol) starts after the window.
+                            Single pairs (of_solve, of_solve_host, n = 1) on the fused engines
+                            only: OF_EINVAL for ALG1, pDR with more sweeps, the plain engine,
+                            batches, the serving loop and the step-level entry points.          */
 } of_params;
 
 typedef struct {
@@ -148,7 +152,8 @@ typedef struct {
     double energy;       /* primal energy eq. (l1:finite) at the output level's last linearisation */
     double dual_value;   /* <It, s> (eq. dual:l1:flow:cons); NaN for pDR and ALG1               */
     float ms;            /* device time of the solve in milliseconds                            */
-    float c;             /* ADMM step c at the end of the solve (params->c unless c_adapt_iters) */
+    float c;             /* the step at the end of the solve: ADMM c, pDR sigma (params->c,
+                            params->sigma unless c_adapt_iters)                                   */
 } of_stats;
 
 /* Fills p with the paper's Sec. 4 settings: pADMM (r = 1), c = 0.05, a = 8, a~ = max M_s,

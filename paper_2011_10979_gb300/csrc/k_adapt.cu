@@ -90,6 +90,42 @@ __global__ void __launch_bounds__(ADAPT_THREADS) k_adapt_residuals(AdaptArgs A) 
     }
 }
 
+// pDR (Sec. 3.1.2 leaves sigma and tau free; the balancing moves their ratio with sigma tau fixed, so
+// T = I - sigma tau Laplace and its SRBGS preconditioner stay the same): the squared changes of the
+// primal block X = (w, u, v) and of the dual block ybar over the step prev -> cur.
+template <typename T, typename TF>
+__global__ void __launch_bounds__(ADAPT_THREADS) k_adapt_pdr_residuals(AdaptArgs A) {
+    __shared__ double sh[32];
+    const int H = A.g.H, W = A.g.W, P = A.g.pitch;
+    double x2 = 0.0, y2 = 0.0;
+    const long long n = (long long)H * W;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const size_t o = (size_t)(q / W) * P + (size_t)(q % W);
+        float xx = 0.f, yy = 0.f;
+#pragma unroll
+        for (int f = F_W; f <= F_V; ++f) {
+            if (f == F_W && !A.has_w) continue;
+            const float e = ldT<TF>(A.cur.f[f], o) - ldT<TF>(A.prev.f[f], o);
+            xx = fmaf(e, e, xx);
+        }
+#pragma unroll
+        for (int f = F_P1; f <= F_Q22; ++f) {
+            if ((f == F_P1 || f == F_P2) && !A.has_w) continue;
+            const float e = ldT<T>(A.cur.f[f], o) - ldT<T>(A.prev.f[f], o);
+            yy = fmaf(e, e, yy);
+        }
+        x2 += xx;
+        y2 += yy;
+    }
+    x2 = block_sum(x2, sh);
+    __syncthreads();
+    y2 = block_sum(y2, sh);
+    if (threadIdx.x == 0) {
+        A.part_r[blockIdx.x] = x2;
+        A.part_d[blockIdx.x] = y2;
+    }
+}
+
 __global__ void __launch_bounds__(ADAPT_THREADS) k_adapt_update(AdaptArgs A, int nb) {
     __shared__ double sh[32];
     double r2 = 0.0, d2 = 0.0;
@@ -101,8 +137,12 @@ __global__ void __launch_bounds__(ADAPT_THREADS) k_adapt_update(AdaptArgs A, int
     __syncthreads();
     d2 = block_sum(d2, sh);
     if (threadIdx.x == 0) {
-        const double r = sqrt(r2), d = sqrt(d2);
         float *c = A.c;
+        double r = sqrt(r2), d = sqrt(d2);
+        if (A.pdr) {  // primal change per unit sigma against dual change per unit tau; *c is theta
+            r /= (double)(A.k.sigma * *c);
+            d /= (double)(A.k.tau / *c);
+        }
         if (r > 10.0 * d) *c = *c * 2.f;
         else if (d > 10.0 * r) *c = *c * 0.5f;
     }
@@ -118,9 +158,13 @@ int adapt_blocks(Geom g) {
     return (int)(b < ADAPT_MAX_BLOCKS ? b : ADAPT_MAX_BLOCKS);
 }
 
-void launch_adapt_c(const AdaptArgs &a, int prec, cudaStream_t s) {
+void launch_adapt_c(const AdaptArgs &a, int prec, int prec_flow, cudaStream_t s) {
     const int nb = adapt_blocks(a.g);
-    TVL1_DISPATCH_PREC(prec, T, k_adapt_residuals<T><<<nb, ADAPT_THREADS, 0, s>>>(a));
+    if (a.pdr) {
+        TVL1_DISPATCH_PREC(prec, T, TVL1_DISPATCH_PREC(prec_flow, TF, k_adapt_pdr_residuals<T, TF><<<nb, ADAPT_THREADS, 0, s>>>(a)));
+    } else {
+        TVL1_DISPATCH_PREC(prec, T, k_adapt_residuals<T><<<nb, ADAPT_THREADS, 0, s>>>(a));
+    }
     k_adapt_update<<<1, ADAPT_THREADS, 0, s>>>(a, nb);
 }
 

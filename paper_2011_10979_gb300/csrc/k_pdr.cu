@@ -349,7 +349,9 @@ __global__ void __launch_bounds__(TileShape<TT>::NT) k_pdr_tile(IterArgs A) {
     const int fi = i0 - 3, fj = j0 - 3;   // global coordinates of frame cell (0, 0)
     const int X[3] = {F_W, F_U, F_V}, XB[3] = {F_WB, F_UB, F_VB};
     const int Y1[3] = {F_P1, F_Q11, F_Q21}, Y2[3] = {F_P2, F_Q12, F_Q22};
-    const float sg = A.k.sigma, ta = A.k.tau, st = sg * ta;
+    float sg, ta;
+    pdr_steps(A.k, A.pairs ? A.pairs[pair].ms_max : A.ms_max, sg, ta);
+    const float st = sg * ta;
     constexpr int C0 = HAS_W ? 0 : 1;
     auto S = [&](int k) { return sm + k * TFN; };
     // frame cell x at offset (li - 3, lj - 3) from the tile's corner; the loops below visit the

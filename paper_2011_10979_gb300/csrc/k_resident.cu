@@ -611,7 +611,9 @@ __global__ void __launch_bounds__(RT, 1) k_pdr_resident(ResArgs A) {
     auto push_s = [&](int k, int li, int j, float v) {
         if (li == nrow - 1 && Gs) Gs[k * PL + j] = v;
     };
-    const float sg = A.k.sigma, ta = A.k.tau, st = A.k.sigma * A.k.tau, beta = A.k.beta, lam = A.k.lambda;
+    float sg, ta;
+    pdr_steps(A.k, A.pairs ? A.pairs[A.list[blockIdx.x / NC]].ms_max : A.ms_max, sg, ta);
+    const float st = sg * ta, beta = A.k.beta, lam = A.k.lambda;
     const int c0 = HAS_W ? 0 : 1;
 
     // ---- load the band; boundary rows of X to both neighbours, the last row of ybar to the south

@@ -171,8 +171,10 @@ of_status validate(const of_params *p, int H, int W) {
     if (p->out_level < 0 || p->out_level >= p->levels) return fail(OF_EINVAL, "out_level must lie in [0, levels)");
     if (p->c_adapt_iters < 0 || p->c_adapt_iters % 10 != 0)
         return fail(OF_EINVAL, "c_adapt_iters must be 0 or a positive multiple of 10");
-    if (p->c_adapt_iters > 0 && (p->method == OF_PDR || p->method == OF_CP))
-        return fail(OF_EINVAL, "c_adapt_iters applies to the ADMM methods only");
+    if (p->c_adapt_iters > 0 && p->method == OF_CP)
+        return fail(OF_EINVAL, "c_adapt_iters applies to the ADMM methods and pDR only");
+    if (p->c_adapt_iters > 0 && p->method == OF_PDR && p->gs_sweeps != 1)
+        return fail(OF_EINVAL, "c_adapt_iters with pDR needs one Gauss-Seidel sweep (its one-launch kernel)");
     if (p->c_adapt_iters > 0 && p->engine == OF_ENGINE_PLAIN)
         return fail(OF_EINVAL, "c_adapt_iters needs a fused engine (the plain engine iterates in place)");
     return OF_OK;
@@ -698,7 +700,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             c.data32[d] = c.A + pl.data32 + d * pl.plane32;
         }
         cudaMemsetAsync(c.misc, 0, sizeof(Misc), s);
-        if (p->c_adapt_iters > 0) launch_c_init(&c.misc->c_cur, p->c, s);
+        if (p->c_adapt_iters > 0) launch_c_init(&c.misc->c_cur, pdr ? 1.f : p->c, s);  // pDR: theta
         for (int l = 1; l < L; ++l) {
             launch_pyr_down((float *)(c.A + pl.img0[l - 1]), geom_of(pl, l - 1), (float *)(c.A + pl.img0[l]),
                             geom_of(pl, l), taps, (float *)(c.A + pl.blur), s);
@@ -769,9 +771,10 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                 pflow = PREC_F32;
             }
             const int start = cur;
-            // adaptive step c (single pair, ADMM): the level's first warp runs its first
-            // c_adapt_iters iterations one streaming launch each and rebalances c after every
-            // 10th; the level's engine then runs the other `rest` iterations with c frozen
+            // adaptive steps (single pair; ADMM: c, pDR: sigma and tau with sigma tau fixed): the
+            // level's first warp runs its first c_adapt_iters iterations one per-iteration launch
+            // each (streaming kernel, pDR tile kernel) and rebalances after every 10th; the level's
+            // engine then runs the other `rest` iterations with the steps frozen
             const int kw = (p->c_adapt_iters > 0 && wp == 0) ? std::min(p->c_adapt_iters, p->iters) : 0;
             const int rest = p->iters - kw;
             if (kw > 0) {
@@ -793,7 +796,12 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                     a.ms_max = &c.misc->ms_max;
                     a.partials = final_it ? c.partials : nullptr;
                     a.tile_h = B.tile_h[l];
-                    launch_admm_fused(a, prec, pflow, s);
+                    if (pdr) {
+                        a.pdr_tile = 1;
+                        launch_pdr_fused(a, prec, pflow, s);
+                    } else {
+                        launch_admm_fused(a, prec, pflow, s);
+                    }
                     if (final_it) launch_sum(c.partials, blocks_of(g, l), &c.misc->res_final, s);
                     if ((it + 1) % 10 == 0) {
                         AdaptArgs d{};
@@ -808,7 +816,8 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         d.part_r = c.partials + mb;
                         d.part_d = c.partials + 2 * mb;
                         d.has_w = has_w;
-                        launch_adapt_c(d, prec, s);
+                        d.pdr = pdr;
+                        launch_adapt_c(d, prec, pflow, s);
                     }
                 }
                 launch_count_iters(&c.misc->iters, nullptr, kw, s);
@@ -1211,7 +1220,8 @@ of_status read_stats(of_ctx *ctx, const Batch &B, int q, const of_params *p, cud
     stats->residual = p->iters > 0 ? sqrt(m.res_final / rows) : 0.0;
     stats->energy = m.energy;
     stats->dual_value = (p->method == OF_PDR || p->method == OF_CP) ? NAN : m.dual;
-    stats->c = p->c_adapt_iters > 0 ? m.c_cur : p->c;
+    const bool adapt = p->c_adapt_iters > 0;
+    stats->c = p->method == OF_PDR ? p->sigma * (adapt ? m.c_cur : 1.f) : adapt ? m.c_cur : p->c;
     if (m.timeout) return fail(OF_ETIMEOUT, "a bounded wait of the persistent engine ran out");
     if (!isfinite(stats->residual) || !isfinite(stats->energy))
         return fail(OF_ENUMERIC, "non-finite residual or energy (NaN/Inf in the inputs or parameters?)");

@@ -66,6 +66,20 @@ __device__ __forceinline__ float a_tilde_of(const Coefs &k, const float *ms_max)
 // solve keeps on the device directly before the pair's ms_max.
 __device__ __forceinline__ float c_of(const Coefs &k, const float *ms_max) { return k.c_dev ? ms_max[-1] : k.c; }
 
+// pDR's steps: sigma and tau of the parameters, or with adaptive steps (sigma theta, tau / theta)
+// with the factor theta (a power of two, so sigma tau stays bitwise the same) kept on the device in
+// the same slot as the adaptive ADMM step.
+__device__ __forceinline__ void pdr_steps(const Coefs &k, const float *ms_max, float &sg, float &ta) {
+    if (k.c_dev) {
+        const float th = ms_max[-1];
+        sg = k.sigma * th;
+        ta = k.tau / th;
+    } else {
+        sg = k.sigma;
+        ta = k.tau;
+    }
+}
+
 }  // namespace tvl1
 
 #define TVL1_DISPATCH_PREC(prec, T, ...)                         \

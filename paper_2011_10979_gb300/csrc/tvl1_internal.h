@@ -253,7 +253,8 @@ void launch_admm_tile2(const IterArgs &a, int ni, int prec, int prec_flow, cudaS
 // Residual balancing of c after one ADMM iteration prev -> cur (both state buffers intact): the
 // constraint residual ||A s + B y|| and the dual residual of the preconditioned ADMM, summed over
 // adapt_blocks(g) blocks into part_r / part_d, then c doubled (||r|| > 10 ||d||) or halved
-// (||d|| > 10 ||r||) in place.  Duals and data in `prec`; the flow fields are not read.
+// (||d|| > 10 ||r||) in place.  Duals and data in `prec`.  pDR (a.pdr): the same rule on
+// ||X^{k+1} - X^k|| / sigma and ||ybar^{k+1} - ybar^k|| / tau, rescaling theta.
 constexpr int ADAPT_MAX_BLOCKS = 1216;
 struct AdaptArgs {
     Geom g{};
@@ -264,9 +265,10 @@ struct AdaptArgs {
     float *c = nullptr;
     double *part_r = nullptr, *part_d = nullptr;  // adapt_blocks(g) slots each
     int has_w = 0;
+    int pdr = 0;      // pDR: *c is theta (sigma theta, tau / theta); the changes of X and ybar
 };
 int adapt_blocks(Geom g);
-void launch_adapt_c(const AdaptArgs &a, int prec, cudaStream_t s);
+void launch_adapt_c(const AdaptArgs &a, int prec, int prec_flow, cudaStream_t s);
 // *c = c0 (one thread): the adapted step starts from the parameter at the start of a solve.
 void launch_c_init(float *c, float c0, cudaStream_t s);
 

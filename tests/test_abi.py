@@ -117,13 +117,14 @@ def test_fields_bytes_covers_every_width_up_to_the_pitch(L):
 
 
 def test_adaptive_step_validation_without_gpu(L):
-    """c_adapt_iters: 0 (the fixed step) or a positive multiple of 10, ADMM methods on the fused
-    engines only."""
+    """c_adapt_iters: 0 (the fixed steps) or a positive multiple of 10; ADMM methods and pDR with one
+    sweep, on the fused engines only."""
     assert flow.default_params().c_adapt_iters == 0
     for ok in (0, 10, 30, 1000):
-        q = flow.default_params(levels=5, c_adapt_iters=ok)
-        assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
-    for bad in (dict(c_adapt_iters=-10), dict(c_adapt_iters=15), dict(c_adapt_iters=20, method=flow.OF_PDR),
+        for m in (flow.OF_PADMM_I, flow.OF_PADMM_II, flow.OF_PDR):
+            q = flow.default_params(levels=5, c_adapt_iters=ok, method=m)
+            assert L.of_arena_bytes(480, 640, ctypes.byref(q)) > 0
+    for bad in (dict(c_adapt_iters=-10), dict(c_adapt_iters=15), dict(c_adapt_iters=20, method=flow.OF_PDR, gs_sweeps=2),
                 dict(c_adapt_iters=20, method=flow.OF_CP), dict(c_adapt_iters=20, engine=flow.OF_ENGINE_PLAIN)):
         q = flow.default_params(levels=5, **bad)
         assert L.of_arena_bytes(480, 640, ctypes.byref(q)) == 0, bad

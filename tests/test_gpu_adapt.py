@@ -137,7 +137,7 @@ def test_adaptive_step_with_16bit_duals(ctx, orc, prec):
 def test_adaptive_step_is_rejected_where_it_does_not_apply(ctx):
     pr = synth.sinusoid_pair()
     I0, I1 = cu(pr.I0), cu(pr.I1)
-    for kw in (dict(c_adapt_iters=15), dict(c_adapt_iters=-10), dict(c_adapt_iters=20, method=flow.OF_PDR),
+    for kw in (dict(c_adapt_iters=15), dict(c_adapt_iters=-10), dict(c_adapt_iters=20, method=flow.OF_PDR, gs_sweeps=2),
                dict(c_adapt_iters=20, method=flow.OF_CP), dict(c_adapt_iters=20, engine=flow.OF_ENGINE_PLAIN)):
         with pytest.raises(flow.OfError) as e:
             flow.of_solve(ctx, I0, I1, flow.default_params(**kw))
@@ -149,3 +149,34 @@ def test_adaptive_step_is_rejected_where_it_does_not_apply(ctx):
     with pytest.raises(flow.OfError) as e:
         flow.of_server_start(ctx, P, 0, 2)
     assert e.value.status == flow.OF_EINVAL
+
+
+# ------------------------------------------------------------------ pDR: sigma and tau, sigma tau fixed
+@pytest.mark.parametrize("engine", ["fused", "stream"])
+@pytest.mark.parametrize("kw", [dict(sigma=32.0, tau=0.025), dict(sigma=0.125, tau=6.4),
+                                dict(sigma=2.0, tau=0.4, beta=0.0)])
+def test_pdr_adaptive_steps_match_the_oracle(ctx, orc, engine, kw):
+    """pDR from a sigma / tau ratio far too large, far too small and the paper's: the window runs on
+    the one-launch tile kernel, the rest of each warp on the level's engine (level-resident on the
+    coarse levels with the fused engine).  The final sigma must be the oracle's (each decision at
+    least 1% from a tie) and the flows meet the schedule bar."""
+    pr = synth.sinusoid_pair()
+    P = dict(method=2, lam=5.0, levels=3, warps=3, iters=40, c_adapt_iters=30, **kw)
+    u, v, st, ru, rv, rst = _both(ctx, orc, pr, P, ENGINES[engine])
+    assert rst["adapt_margin"] > MARGIN, rst["adapt_margin"]
+    assert st["c"] == pytest.approx(rst["c_final"], rel=1e-6)
+    du, dv = np.abs(u - ru), np.abs(v - rv)
+    assert du.max() <= 1e-3 and dv.max() <= 1e-3 and np.hypot(u - ru, v - rv).mean() <= 1e-2
+    assert st["iters_run"] == rst["iters_run"]
+
+
+def test_pdr_adaptive_engines_agree_bitwise(ctx):
+    pr = synth.random_affine_rect_pair(150, 210, 5)
+    out = []
+    for eng in (flow.OF_ENGINE_FUSED, flow.OF_ENGINE_STREAM, flow.OF_ENGINE_RESIDENT):
+        P = flow.default_params(method=flow.OF_PDR, lam=5.0, levels=3, warps=2, iters=40, sigma=32.0, tau=0.025,
+                                c_adapt_iters=20, engine=eng)
+        u, v, _, st = flow.of_solve(ctx, cu(pr.I0), cu(pr.I1), P)
+        out.append((u, v, st["c"]))
+    for u, v, c in out[1:]:
+        assert torch.equal(u, out[0][0]) and torch.equal(v, out[0][1]) and c == out[0][2]
