@@ -302,11 +302,18 @@ bool admm_tile2_of(const of_params *p, bool batched, Geom g) {
            (long)g.H * g.W <= TILE2_MAX_PX;
 }
 
-bool use_resident(const of_params *p, Geom g) {
+// Levels up to this many pixels run the ADMM methods level-resident when the several-iterations
+// tile kernel is the alternative (measured per iteration, resident against tile kernel: 1.06 /
+// 1.96 us at 40x30, 1.36 / 2.15 at 80x60, 1.94 / 2.14 at 120x90, 2.67 / 2.14 at 160x120); against
+// the row-streaming kernel the resident launch wins up to 32,000 px.
+constexpr long TILE_RESIDENT_MAX_PX = 12000;
+
+bool use_resident(const of_params *p, Geom g, bool batched = false) {
     if (!admm_resident_fits(g, p->method)) return false;
     if (p->engine == OF_ENGINE_RESIDENT) return true;
     if (p->engine != OF_ENGINE_FUSED && p->engine != OF_ENGINE_PERSISTENT) return false;
     if (pdr_tile_of(p)) return (long)g.H * g.W <= PDR_TILE_RESIDENT_MAX_PX;
+    if (admm_tile2_of(p, batched, g)) return (long)g.H * g.W <= TILE_RESIDENT_MAX_PX;
     return admm_resident_preferred(g, p->method);
 }
 
@@ -455,13 +462,13 @@ Batch make_batch(int n, const int *H, const int *W, const of_params *p) {
             // clusters run at once; otherwise one work-list launch per iteration serves them better
             B.res[l].assign(n, 0);
             int elig = 0;
-            for (int k = 0; k < n; ++k) elig += use_resident(p, geom_of(B.pl[k], l)) ? 1 : 0;
+            for (int k = 0; k < n; ++k) elig += use_resident(p, geom_of(B.pl[k], l), true) ? 1 : 0;
             const bool take = elig > 0 && elig <= admm_resident_max_clusters();
             for (int k = 0; k < n; ++k) {
                 const Geom g = geom_of(B.pl[k], l);
                 if (g.H > gm.H) gm.H = g.H;
                 if (g.W > gm.W) gm.W = g.W;
-                if (take && use_resident(p, g)) {
+                if (take && use_resident(p, g, true)) {
                     B.res[l][k] = 1;
                     ++B.nres[l];
                     B.res_nc[l] = std::max(B.res_nc[l], admm_resident_nc(g, p->method));
