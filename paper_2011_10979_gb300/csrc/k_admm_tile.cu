@@ -1,22 +1,21 @@
-// k_admm_tile.cu -- two ADMM inner iterations (Sec. 3.1.1, eq. rpADMMI / rpADMMII / Zach-pADMM) in
-// one launch, for the single-pair levels that run on the per-iteration engines with a fixed
-// schedule (no stopping test): each block owns a TT x TT tile of output pixels and stages in
-// shared memory what two iterations need around it.
+// k_admm_tile.cu -- several ADMM inner iterations (Sec. 3.1.1, eq. rpADMMI / rpADMMII /
+// Zach-pADMM) in one launch, for the single-pair levels that run on the per-iteration engines with
+// a fixed schedule (no stopping test): each block owns a TT x TT tile of output pixels and stages
+// in shared memory what the iterations need around it.
 //
 // One iteration at an output pixel needs y^{k+1} one pixel west and north (div y^{k+1}), y^{k+1}
 // at a pixel needs div y^k, s, Lambda and the data one pixel east and south, and div y^k needs
-// y^k one pixel west and north.  Two iterations chain that twice, so the block stages a
-// (TT + 5)^2 frame starting 3 pixels above and left of the tile: y^k on the whole frame (offsets
-// -3 .. TT + 1 from the tile's corner), s, Lambda, Ix, Iy on -2 .. TT + 1 and It on -1 .. TT, then
-// runs, between block barriers,
-//   iteration k:   div y^k on -2 .. TT + 1, y^{k+1} on -2 .. TT, s^{k+1} and Lambda^{k+1} on -1 .. TT;
-//   iteration k+1: div y^{k+1} on -1 .. TT, y^{k+2} on -1 .. TT - 1, and the finish on the tile,
-//                  which stores the state and the squared residual.
+// y^k one pixel west and north.  NI iterations (2 or 3) chain that NI times, so the block stages a
+// (TT + 2 NI + 1)^2 frame starting NI + 1 pixels above and left of the tile: y^k on the whole
+// frame, s, Lambda, Ix, Iy without its first row and column, and It where the finishes need it.
+// Then, between block barriers, on squares that shrink by one pixel per iteration: div y^k; per
+// iteration the y update, then s, Lambda and the next iteration's div y on the region it needs it
+// on; the last iteration's finish on the tile stores the state and the squared residual.
 // The per-pixel arithmetic is that of the streaming kernel (k_admm_math.cuh), and the state
-// between the two iterations is rounded to its storage type exactly where the streaming kernel's
-// stores round it (y^{k+1} when read as y, s and Lambda when written), so two iterations here are
-// bitwise two launches of the streaming kernel.  The launch reads one state buffer and writes the
-// other; the residual's partial sums are those of the second iteration, grouped per tile.
+// between the iterations is rounded to its storage type exactly where the streaming kernel's
+// stores round it (y^{k+1} when read as y, s and Lambda when written), so NI iterations here are
+// bitwise NI launches of the streaming kernel.  The launch reads one state buffer and writes the
+// other; the residual's partial sums are those of the last iteration, grouped per tile.
 #include <math.h>
 
 #include <mutex>
@@ -92,16 +91,14 @@ __global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
     };
     // y as the streaming kernel reads it: the stored value, rounded to the storage type
     auto Y = [&](int k, int x) { return storage_round<T>(S(SY0 + k)[x]); };
-    // ---- div y on a square (from y rounded to storage)
-    auto div_phase = [&](auto LO_, auto HI_) {
-        for_cells(LO_, HI_, [&](int x, int i, int j) {
-            const bool ex = j < W - 1, wx = j > 0, ey = i < H - 1, ny = i > 0;
-            float dp = 0.f;
-            if (HAS_W) dp = div2(ex ? Y(0, x) : 0.f, wx ? Y(0, x - 1) : 0.f, ey ? Y(1, x) : 0.f, ny ? Y(1, x - FS) : 0.f);
-            S(SDP)[x] = dp;
-            S(SDP + 1)[x] = div2(ex ? Y(2, x) : 0.f, wx ? Y(2, x - 1) : 0.f, ey ? Y(3, x) : 0.f, ny ? Y(3, x - FS) : 0.f);
-            S(SDP + 2)[x] = div2(ex ? Y(4, x) : 0.f, wx ? Y(4, x - 1) : 0.f, ey ? Y(5, x) : 0.f, ny ? Y(5, x - FS) : 0.f);
-        });
+    // ---- div y at a pixel (from y rounded to storage), stored for the next y phase
+    auto div_store = [&](int x, int i, int j) {
+        const bool ex = j < W - 1, wx = j > 0, ey = i < H - 1, ny = i > 0;
+        float dp = 0.f;
+        if (HAS_W) dp = div2(ex ? Y(0, x) : 0.f, wx ? Y(0, x - 1) : 0.f, ey ? Y(1, x) : 0.f, ny ? Y(1, x - FS) : 0.f);
+        S(SDP)[x] = dp;
+        S(SDP + 1)[x] = div2(ex ? Y(2, x) : 0.f, wx ? Y(2, x - 1) : 0.f, ey ? Y(3, x) : 0.f, ny ? Y(3, x - FS) : 0.f);
+        S(SDP + 2)[x] = div2(ex ? Y(4, x) : 0.f, wx ? Y(4, x - 1) : 0.f, ey ? Y(5, x) : 0.f, ny ? Y(5, x - FS) : 0.f);
     };
     // ---- y^{k+1} on a square, in place (only the pixel itself reads its y here)
     auto y_phase = [&](auto LO_, auto HI_) {
@@ -154,13 +151,15 @@ __global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
         dq2n = div2(ex ? S(SY0 + 4)[x] : 0.f, wx ? S(SY0 + 4)[x - 1] : 0.f, hy ? S(SY0 + 5)[x] : 0.f,
                     nyy ? S(SY0 + 5)[x - FS] : 0.f);
     };
-    // ---- iterations k .. k + NI - 2: an iteration E pixels from the last one computes div y on
-    // -1 - E .. TT + E, y on -1 - E .. TT - 1 + E, and s, Lambda (rounded as stored; only the pixel
-    // itself reads them in that phase) on -E .. TT - 1 + E
+    // ---- iterations k .. k + NI - 2: an iteration E pixels from the last one computes y on
+    // -1 - E .. TT - 1 + E, then on -E .. TT - 1 + E s and Lambda (rounded as stored; only the
+    // pixel itself reads them in that phase) and, for the next iteration, div y^{k+1} -- the
+    // region the next iteration needs it on, so no phase of its own.  The first iteration's div y^k
+    // comes from the staged y.
+    for_cells(IC<-NI>{}, IC<TT + NI - 1>{}, div_store);
+    __syncthreads();
     auto iteration = [&](auto E_) {
         constexpr int e = decltype(E_)::value;
-        div_phase(IC<-1 - e>{}, IC<TT + e>{});
-        __syncthreads();
         y_phase(IC<-1 - e>{}, IC<TT - 1 + e>{});
         __syncthreads();
         for_cells(IC<-e>{}, IC<TT - 1 + e>{}, [&](int x, int i, int j) {
@@ -173,14 +172,19 @@ __global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
             if (HAS_W) S(SW_)[x] = storage_round<TF>(w);
             S(SU)[x] = storage_round<TF>(u);
             S(SV)[x] = storage_round<TF>(v);
+            if (std::is_same<T, float>::value) {  // y as stored is y: the finish's div is the next one
+                S(SDP)[x] = dpn;
+                S(SDP + 1)[x] = dq1n;
+                S(SDP + 2)[x] = dq2n;
+            } else {
+                div_store(x, i, j);
+            }
         });
         __syncthreads();
     };
     if constexpr (NI >= 3) iteration(IC<2>{});
     iteration(IC<1>{});
     // ---- the last iteration: its finish on the tile stores the state
-    div_phase(IC<-1>{}, IC<TT>{});
-    __syncthreads();
     y_phase(IC<-1>{}, IC<TT - 1>{});
     __syncthreads();
     float res = 0.f;
