@@ -292,7 +292,7 @@ constexpr long PDR_TILE_RESIDENT_MAX_PX = 12000;
 // there, where the tiles' 34% larger staged frame costs more than the saved launch).
 constexpr long TILE2_MAX_PX = 320000;
 // Iterations per launch (the last launch of a warp may run 2, or 1).  Measured per iteration at
-// 640x480 / 320x240: 7.86 / 3.21 us with 2, 7.36 / 3.04 with 3, 7.88 / 3.29 with 4 (a 41 x 41
+// 640x480 / 320x240: 7.86 / 3.21 us with 2, 6.72 / 2.78 with 3, 7.13 / 3.01 with 4 (a 41 x 41
 // frame: 64 registers and 108 KB of shared memory per block, and a third more halo work).
 constexpr int TILE_ITERS = 3;
 
