@@ -292,11 +292,9 @@ __global__ void k_pdr_finish(IterArgs A) {
 // one pixel around, which need first red values one more pixel around, which need X^k (the old
 // black values) and b one more; b needs ybar one pixel west and north.  So the block stages, in
 // a (TT + 7)^2 frame starting 3 pixels above and left of the tile, X^k on the whole frame, ybar on
-// offsets -3 .. TT + 2 and Xbar on -2 .. TT + 2, and runs three stages between block barriers: the
-// first red half-sweep on -2 .. TT + 2 (forming b there, kept for the second red update), black on
-// -1 .. TT + 1 (forming its own b), and on the tile the second red update -- a black pixel's thread
-// forms its red east and south neighbours' values itself -- with the Xbar / ybar updates and the
-// stores.  Each stage's
+// offsets -3 .. TT + 2 and Xbar on -2 .. TT + 2, and runs the stages on shrinking squares between
+// block barriers: b and the first red half-sweep on -2 .. TT + 2, black on -1 .. TT + 1, the
+// second red on 0 .. TT, then the Xbar / ybar updates and the stores on the tile.  Each stage's
 // arithmetic and rounding (X rounded to its storage type after every half-sweep, b in FP32) is
 // that of the per-kernel engine, so the flows are bitwise equal; the residual's partial sums are
 // grouped per tile.
@@ -400,29 +398,20 @@ __global__ void __launch_bounds__(TileShape<TT>::NT) k_pdr_tile(IterArgs A) {
     }
     __syncthreads();
     using I = int;
-    // b_c = Xbar_c + sigma div ybar_c at a pixel (a pure function of the staged values, so every
-    // stage that needs it forms it itself)
-    auto rhs = [&](int c, int x, int i, int j) {
-        const float *a = S(TY0 + 2 * c), *b = S(TY0 + 2 * c + 1);
-        const float d = (((j < W - 1 ? a[x] : 0.f) - (j > 0 ? a[x - 1] : 0.f)) + (i < H - 1 ? b[x] : 0.f)) -
-                        (i > 0 ? b[x - TFS] : 0.f);
-        return pdr_rhs(S(TXB0 + c)[x], d, sg);
-    };
-    // one Gauss-Seidel update of component c at a pixel from right-hand side bv and the current X of
-    // its in-domain neighbours (west, east, north, south), rounded to the flow storage type
-    auto gs_at = [&](int c, int x, int i, int j, float bv) {
-        const float *xc = S(TX0 + c);
-        const bool hw = j > 0, he = j < W - 1, hn_ = i > 0, hs = i < H - 1;
-        float acc = 0.f;
-        if (hw) acc += xc[x - 1];
-        if (he) acc += xc[x + 1];
-        if (hn_) acc += xc[x - TFS];
-        if (hs) acc += xc[x + TFS];
-        return storage_round<TF>(pdr_gs(bv, acc, (int)hw + (int)he + (int)hn_ + (int)hs, st));
-    };
-    // a half-sweep of the pixels of colour `colour` (only those are visited) in the square of offsets
-    // [LO, HI], in place; keep_b: also store b, which the second red update needs
-    auto half_sweep = [&](auto LO_, auto HI_, int colour, bool keep_b) {
+    // ---- b = Xbar + sigma div ybar on offsets -2 .. TT + 2
+    for_cells(std::integral_constant<I, -2>{}, std::integral_constant<I, TT + 2>{}, [&](int x, int i, int j) {
+#pragma unroll
+        for (int c = C0; c < 3; ++c) {
+            const float *a = S(TY0 + 2 * c), *b = S(TY0 + 2 * c + 1);
+            const float d = (((j < W - 1 ? a[x] : 0.f) - (j > 0 ? a[x - 1] : 0.f)) + (i < H - 1 ? b[x] : 0.f)) -
+                            (i > 0 ? b[x - TFS] : 0.f);
+            S(TB0 + c)[x] = pdr_rhs(S(TXB0 + c)[x], d, sg);
+        }
+    });
+    __syncthreads();
+    // one Gauss-Seidel update of the pixels of colour `colour` (only those are visited) in the square
+    // of offsets [LO, HI], in place, rounded to the flow storage type
+    auto half_sweep = [&](auto LO_, auto HI_, int colour) {
         constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1, hn = (n + 1) / 2;
         for (int t = threadIdx.x; t < n * hn; t += TNT) {
             const int r = t / hn, k = t % hn;
@@ -432,35 +421,39 @@ __global__ void __launch_bounds__(TileShape<TT>::NT) k_pdr_tile(IterArgs A) {
             const int i = fi + li, j = fj + lj;
             if (!(i >= 0 && i < H && j >= 0 && j < W)) continue;
             const int x = li * TFS + lj;
+            const bool hw = j > 0, he = j < W - 1, hn_ = i > 0, hs = i < H - 1;
+            const int nb = (int)hw + (int)he + (int)hn_ + (int)hs;
 #pragma unroll
             for (int c = C0; c < 3; ++c) {
-                const float bv = rhs(c, x, i, j);
-                if (keep_b) S(TB0 + c)[x] = bv;
-                S(TX0 + c)[x] = gs_at(c, x, i, j, bv);
+                const float *xc = S(TX0 + c);
+                float acc = 0.f;
+                if (hw) acc += xc[x - 1];
+                if (he) acc += xc[x + 1];
+                if (hn_) acc += xc[x - TFS];
+                if (hs) acc += xc[x + TFS];
+                S(TX0 + c)[x] = storage_round<TF>(pdr_gs(S(TB0 + c)[x], acc, nb, st));
             }
         }
     };
-    half_sweep(std::integral_constant<I, -2>{}, std::integral_constant<I, TT + 2>{}, 0, true);
+    half_sweep(std::integral_constant<I, -2>{}, std::integral_constant<I, TT + 2>{}, 0);
     __syncthreads();
-    half_sweep(std::integral_constant<I, -1>{}, std::integral_constant<I, TT + 1>{}, 1, false);
+    half_sweep(std::integral_constant<I, -1>{}, std::integral_constant<I, TT + 1>{}, 1);
     __syncthreads();
-    // ---- the tile: the second red update (a black pixel's thread forms its red east and south
-    // neighbours' values itself, as their own threads do, instead of a phase of their own), the
-    // Xbar and ybar updates, stores, residual ||X^{k+1} - X^k||^2
+    half_sweep(std::integral_constant<I, 0>{}, std::integral_constant<I, TT>{}, 0);
+    __syncthreads();
+    // ---- the tile: Xbar and ybar updates, stores, residual ||X^{k+1} - X^k||^2
     double res = 0.0;
     const float beta = A.k.beta, lam = A.k.lambda;
-    auto x_new = [&](int c, int x, int i, int j) {
-        return ((i + j) & 1) == 0 ? gs_at(c, x, i, j, S(TB0 + c)[x]) : S(TX0 + c)[x];
-    };
     for_cells(std::integral_constant<I, 0>{}, std::integral_constant<I, TT - 1>{}, [&](int x, int i, int j) {
         const size_t o = (size_t)i * P + j;
         const bool hx = j < W - 1, hy = i < H - 1;
         float xv[3] = {0.f, 0.f, 0.f}, g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int c = C0; c < 3; ++c) {
-            xv[c] = x_new(c, x, i, j);
-            g[2 * c] = hx ? x_new(c, x + 1, i, j + 1) - xv[c] : 0.f;
-            g[2 * c + 1] = hy ? x_new(c, x + TFS, i + 1, j) - xv[c] : 0.f;
+            const float *xc = S(TX0 + c);
+            xv[c] = xc[x];
+            g[2 * c] = hx ? xc[x + 1] - xv[c] : 0.f;
+            g[2 * c + 1] = hy ? xc[x + TFS] - xv[c] : 0.f;
         }
         const float ix = ldT<T>(Ixp, o), iy = ldT<T>(Iyp, o), it = ldT<T>(Itp, o);
         float xb[3] = {S(TXB0)[x], S(TXB0 + 1)[x], S(TXB0 + 2)[x]};
