@@ -1,7 +1,7 @@
 // k_admm_tile.cu -- several ADMM inner iterations (Sec. 3.1.1, eq. rpADMMI / rpADMMII /
-// Zach-pADMM) in one launch, for the single-pair levels that run on the per-iteration engines with
-// a fixed schedule (no stopping test): each block owns a TT x TT tile of output pixels and stages
-// in shared memory what the iterations need around it.
+// Zach-pADMM) in one launch, for the single-pair levels that run on the per-iteration engines
+// (with the stopping test, the tested iterations run on the streaming kernel): each block owns a
+// TT x TT tile of output pixels and stages in shared memory what the iterations need around it.
 //
 // One iteration at an output pixel needs y^{k+1} one pixel west and north (div y^{k+1}), y^{k+1}
 // at a pixel needs div y^k, s, Lambda and the data one pixel east and south, and div y^k needs
@@ -29,34 +29,38 @@ namespace tvl1 {
 namespace {
 
 enum { SY0 = 0, SS = 6, SW_ = 7, SU = 8, SV = 9, SIX = 10, SIY = 11, SIT = 12, SDP = 13, NPL = 16 };
-// NI iterations per launch on TT x TT tiles: the frame spans offsets -NI - 1 .. TT + NI - 1.
+// NI iterations per launch on TT x TT tiles: the frame spans offsets -NI - 1 .. TT + NI - 1, FS
+// cells a side (FC in all), a plane row FS floats.  512 threads for both tile sizes (measured per
+// iteration with 16-pixel tiles, 256 against 512 threads: 2.66 / 2.38 us at 320x240, 2.00 / 1.59
+// at 160x120, where the blocks do not fill the GPU and each phase's latency is the bound).
 template <int TT, int NI> struct Shape {
-    static constexpr int FS = TT + 2 * NI + 1, FN = FS * FS, NT = TT == 32 ? 512 : 256, SMEM = NPL * FN * 4;
+    static constexpr int FS = TT + 2 * NI + 1, FC = FS * FS, NT = 512, SMEM = NPL * FC * 4;
 };
 
 template <int N> using IC = std::integral_constant<int, N>;
 
 template <typename T, typename TF, bool HAS_W, int VARIANT, int TT, int NI>
 __global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
-    constexpr int FS = Shape<TT, NI>::FS, FN = Shape<TT, NI>::FN, NT = Shape<TT, NI>::NT, OFF = NI + 1;
+    using SH = Shape<TT, NI>;
+    constexpr int FS = SH::FS, FC = SH::FC, NT = SH::NT, OFF = NI + 1;
     extern __shared__ float sm[];
     __shared__ double red[32];
     const int H = A.g.H, W = A.g.W, P = A.g.pitch;
     if (A.done && *A.done) return;
     const int i0 = blockIdx.y * TT, j0 = blockIdx.x * TT;
     const int fi = i0 - OFF, fj = j0 - OFF;  // global coordinates of frame cell (0, 0)
-    auto S = [&](int k) { return sm + k * FN; };
+    auto S = [&](int k) { return sm + k * FC; };
     const int YF[6] = {F_P1, F_P2, F_Q11, F_Q12, F_Q21, F_Q22};
     // ---- stage the frame; all of a thread's loads are issued before its shared-memory stores
     {
-        constexpr int NP = (FN + NT - 1) / NT;
+        constexpr int NP = (FC + NT - 1) / NT;
         float v[NP][13];
 #pragma unroll
         for (int r = 0; r < NP; ++r) {
             const int x = threadIdx.x + r * NT;
             const int li = x / FS, lj = x % FS;
             const int i = fi + li, j = fj + lj;
-            const bool ok = x < FN && i >= 0 && i < H && j >= 0 && j < W;
+            const bool ok = x < FC && i >= 0 && i < H && j >= 0 && j < W;
             const bool ok2 = ok && li >= 1 && lj >= 1;
             const bool ok3 = ok2 && li >= 2 && lj >= 2 && li <= FS - 2 && lj <= FS - 2;
             const size_t o = ok ? (size_t)i * P + j : 0;
@@ -73,20 +77,51 @@ __global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
 #pragma unroll
         for (int r = 0; r < NP; ++r) {
             const int x = threadIdx.x + r * NT;
-            if (x >= FN) continue;
+            if (x >= FC) continue;
 #pragma unroll
             for (int k = 0; k < 13; ++k) S(k)[x] = v[r][k];
         }
     }
     const StepK K = step_coefs(A.k, a_tilde_of(A.k, A.ms_max), c_of(A.k, A.ms_max));
     __syncthreads();
-    // the in-image cells of the square of offsets [LO, HI] (compile-time bounds)
+    // the in-image cells of the square of offsets [LO, HI] (compile-time bounds, n >= TT a side).
+    // 32 consecutive cells of the square would straddle two of its rows, FS - n floats apart, and
+    // most warps would meet a two-way bank conflict on every shared-memory access.  Instead:
+    //  - 16-pixel tiles (FS = 21 or 23): lane t of the run covers frame offset t from the square's
+    //    first cell, rows counted at the frame pitch, so a warp's addresses are consecutive; the
+    //    FS - n cells past each row's end idle their lanes (over a 22-cell square with FS = 23,
+    //    16 wavefronts per access to a plane against 31);
+    //  - 32-pixel tiles: a warp task is a whole row of the square's first 32 columns (consecutive
+    //    addresses) or a run of 32 cells of its remaining n - 32 columns, row by row (at most
+    //    two-way conflicts there).  Measured per iteration at 640x480: 6.72 us with consecutive
+    //    cells of the square, 5.48 pitch-wrapped, 5.41 with row tasks.
+    // The east, west, north and south neighbours of the cells a warp touches fall in the same
+    // number of banks as the cells themselves.
     auto for_cells = [&](auto LO_, auto HI_, auto &&f) {
-        constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1;
-        for (int t = threadIdx.x; t < n * n; t += NT) {
-            const int li = lo + OFF + t / n, lj = lo + OFF + t % n;
-            const int i = fi + li, j = fj + lj;
-            if (i >= 0 && i < H && j >= 0 && j < W) f(li * FS + lj, i, j);
+        constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1, x0 = (lo + OFF) * (FS + 1);
+        static_assert(n >= TT, "square narrower than a tile");
+        if constexpr (TT == 16) {
+            for (int t = threadIdx.x; t < (n - 1) * FS + n; t += NT) {
+                const int r = t / FS, c = t % FS;
+                const int i = fi + lo + OFF + r, j = fj + lo + OFF + c;
+                if (c < n && i >= 0 && i < H && j >= 0 && j < W) f(x0 + t, i, j);
+            }
+        } else {
+            constexpr int M = n - TT, NTASK = n + (n * M + 31) / 32;
+            const int lane = threadIdx.x & 31;
+            for (int task = threadIdx.x >> 5; task < NTASK; task += NT / 32) {
+                int r = task, c = lane;
+                if constexpr (M > 0) {
+                    if (task >= n) {
+                        const int q = (task - n) * 32 + lane;
+                        if (q >= n * M) continue;
+                        r = q / M;
+                        c = TT + q % M;
+                    }
+                }
+                const int i = fi + lo + OFF + r, j = fj + lo + OFF + c;
+                if (i >= 0 && i < H && j >= 0 && j < W) f(x0 + r * FS + c, i, j);
+            }
         }
     };
     // y as the streaming kernel reads it: the stored value, rounded to the storage type

@@ -284,9 +284,8 @@ bool pdr_tile_of(const of_params *p) {
 // 2.7 / 4.3 at 80x60, 4.3 / 4.3 at 120x90, 6.0 / 4.4 at 160x120).
 constexpr long PDR_TILE_RESIDENT_MAX_PX = 12000;
 
-// Whether a single pair's streamed ADMM level runs two iterations per launch (k_admm_tile.cu): a
-// fixed schedule (the stopping test needs the state after every tenth iteration in a known buffer),
-// the built-in strip rule (a pinned or autotuned height asks for the row-streaming kernel), and a
+// Whether a single pair's streamed ADMM level runs several iterations per launch (k_admm_tile.cu):
+// the built-in strip rule (a pinned or autotuned height asks for the row-streaming kernel) and a
 // level whose state stays in L2.  Measured per iteration against the row-streaming kernel: 320x240
 // 3.21 against 3.99 us, 640x480 7.86 against 7.98; but 1920x1080 52.0 against 39.6 (DRAM-bound
 // there, where the tiles' 34% larger staged frame costs more than the saved launch).
@@ -297,16 +296,15 @@ constexpr long TILE2_MAX_PX = 320000;
 constexpr int TILE_ITERS = 3;
 
 bool admm_tile2_of(const of_params *p, bool batched, Geom g) {
-    return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->tol == 0.0 &&
-           p->rows_per_warp == 0 && (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM) &&
+    return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->rows_per_warp == 0 && (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM) &&
            (long)g.H * g.W <= TILE2_MAX_PX;
 }
 
 // Levels up to this many pixels run the ADMM methods level-resident when the several-iterations
-// tile kernel is the alternative (measured per iteration, resident against tile kernel: 1.06 /
-// 1.96 us at 40x30, 1.36 / 2.15 at 80x60, 1.94 / 2.14 at 120x90, 2.67 / 2.14 at 160x120); against
+// tile kernel is the alternative (measured per iteration, resident against tile kernel: 1.04 /
+// 1.51 us at 40x30, 1.34 / 1.58 at 80x60, 1.93 / 1.58 at 120x90, 2.67 / 1.61 at 160x120); against
 // the row-streaming kernel the resident launch wins up to 32,000 px.
-constexpr long TILE_RESIDENT_MAX_PX = 12000;
+constexpr long TILE_RESIDENT_MAX_PX = 7000;
 
 bool use_resident(const of_params *p, Geom g, bool batched = false) {
     if (!admm_resident_fits(g, p->method)) return false;
@@ -896,12 +894,24 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
             // the non-resident pairs (ALG1)
             const bool streamed = !persl && (batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1);
-            // single pair, ADMM, fixed schedule, the built-in strip rule: two iterations per launch
+            // single pair, ADMM, the built-in strip rule: several iterations per launch.  With the
+            // stopping test every ten iterations run as launches of 3, 3, 3 and 1: the tested state
+            // is a single-iteration launch's (its residual partials), an even number of launches
+            // leaves it in bufs[start2] as on the one-launch-per-iteration path, and the warp's last
+            // launch is a single iteration too, so the final residual sums the same partials
+            // whether or not the test stopped the warp.
             const bool tile2 = streamed && admm_tile2_of(p, batched, geom_of(*pc[0].pl, l));
-            int par = start2, last_nb = 0;  // the two-iteration path's buffer parity and last block count
+            int par = start2, last_nb = 0;  // the several-iterations path's buffer parity and last block count
             for (int it = 0, step = 1; streamed && it < rest; it += step) {
-                step = tile2 ? std::min(TILE_ITERS, rest - it) : 1;
-                const bool check = p->tol > 0.0 && (it + 1) % 10 == 0;
+                step = 1;
+                if (tile2) {
+                    step = std::min(TILE_ITERS, rest - it);
+                    if (p->tol > 0.0) {
+                        step = std::min(step, 10 - it % 10);
+                        if (step > 1 && it + step == rest) --step;
+                    }
+                }
+                const bool check = p->tol > 0.0 && (it + step) % 10 == 0;
                 const bool final_it = last_warp && it + step == rest;
                 IterArgs a{};
                 a.k = k;
@@ -937,7 +947,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         last_nb = blocks_of(g, l);
                     }
                     if (check) {
-                        const int nb = blocks_of(g, l);
+                        const int nb = step > 1 ? admm_tile2_blocks(g) : blocks_of(g, l);
                         const double rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
                         launch_reduce_check(c.partials, nb, &c.misc->res_check, rows, p->tol, &c.misc->done,
                                             &c.misc->iters, 10, s);
@@ -982,7 +992,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             }
             if (pingpong) {
                 const int fin = tile2 ? par : (start + p->iters) & 1;
-                if (p->tol > 0.0 && (rest & 1))
+                if (p->tol > 0.0 && (tile2 ? par != start2 : (rest & 1)))
                     for (int q = 0; q < n; ++q)
                         if (!(res1 || (batched && B.res[l][q])))  // the resident engine writes buf[fin] itself
                             launch_parity_fix(bufs_of(pc[q])[start2], bufs_of(pc[q])[fin], geom_of(*pc[q].pl, l),

@@ -107,9 +107,9 @@ def test_batch_every_height_equals_single(ctx, ty):
 def test_autotuned_single_pair(ctx):
     """640 x 480, 5 levels, default engine: the two levels above the resident size are tuned to
     one of the kernel's heights and the three resident levels report 0; the tuned solve equals the
-    built-in rule's bit for bit and the tuning is kept by the context.  The built-in rule with a
-    fixed schedule runs the tile kernel (three iterations per launch) on the three levels above
-    12,000 px (the 160x120 level included), so it launches fewer kernels."""
+    built-in rule's bit for bit and the tuning is kept by the context.  The built-in rule runs the
+    tile kernel (three iterations per launch) on the three levels above 7,000 px (the 160x120
+    level included), so it launches fewer kernels."""
     P = flow.default_params(lam=5.0, levels=5, warps=2, iters=10, rows_per_warp=-1)
     rows = flow.of_rows_per_warp(ctx, [(480, 640)], P)
     assert rows[0] in HEIGHTS and rows[1] in HEIGHTS and rows[2:] == [0, 0, 0]

@@ -3,7 +3,8 @@ one; single pairs with a fixed schedule and the built-in strip rule) against one
 iteration of the row-streaming kernel (a pinned strip height) and the persistent engine: the state
 between the iterations is rounded where the streaming kernel's stores round it, so the flows are
 bitwise equal, on tiles with ragged edges, both tile sizes, every ADMM variant, 16-bit storage and
-iteration counts that end a warp with launches of one, two and three iterations."""
+iteration counts that end a warp with launches of one, two and three iterations, with and without
+the stopping test."""
 import numpy as np
 import pytest
 
@@ -76,17 +77,45 @@ def test_whole_solve_against_the_persistent_engine(ctx):
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
 
 
-def test_stopping_rule_and_pinned_heights_keep_one_launch_per_iteration(ctx):
-    """tol > 0 (the test needs each tenth iteration's state) and a pinned height run the
-    row-streaming kernel; the flows still equal the tile path's where the schedule runs in
-    full."""
-    P = flow.default_params(lam=5.0, levels=1, warps=1, iters=40, engine=flow.OF_ENGINE_STREAM)
-    n_two = flow.of_solve_kernel_count(ctx, 480, 640, P)
-    P.tol = 1e-30   # never met: the full schedule, one launch per iteration
-    n_tol = flow.of_solve_kernel_count(ctx, 480, 640, P)
-    assert n_tol > n_two + 15
-    pr = synth.affine_rect_pair()
-    a = _solve(ctx, pr, lam=5.0, levels=1, warps=1, iters=40, engine=flow.OF_ENGINE_STREAM)
-    b = _solve(ctx, pr, lam=5.0, levels=1, warps=1, iters=40, engine=flow.OF_ENGINE_STREAM, tol=1e-30)
-    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
-    assert a[3]["iters_run"] == b[3]["iters_run"] == 40
+def _tol_met_at_20(ctx, pr, kw):
+    """A tolerance the residual meets at the check after iteration 20 of a one-warp solve (or at
+    the one after iteration 10)."""
+    k = dict(kw, warps=1, iters=20, rows_per_warp=2)
+    return _solve(ctx, pr, **k)[3]["residual"] * 1.001
+
+
+@pytest.mark.parametrize("H,W", [(37, 53), (203, 333), (480, 640)])
+@pytest.mark.parametrize("iters", [40, 25, 27, 23])
+@pytest.mark.parametrize("stop", ["never", "met"])
+def test_stopping_rule_on_the_tile_path(ctx, H, W, iters, stop):
+    """tol > 0 on the several-iterations path (launches of 3, 3, 3 and 1 per ten iterations, the
+    warp's last launch a single iteration) against one launch per iteration: bitwise equal flows
+    and the same iterations run, whether the test stops a warp early (the tails
+    of 25 and 27 iterations leave an odd number of launches, so the stopped state is copied to the
+    final buffer) or never."""
+    pr = _pair(H, W, 11 + W)
+    kw = dict(lam=2.0, levels=1, warps=2, iters=iters, engine=flow.OF_ENGINE_STREAM)
+    tol = 1e-30 if stop == "never" else _tol_met_at_20(ctx, pr, kw)
+    u0, v0, w0, s0 = _solve(ctx, pr, rows_per_warp=2, tol=tol, **kw)
+    u1, v1, w1, s1 = _solve(ctx, pr, rows_per_warp=0, tol=tol, **kw)
+    assert torch.equal(u0, u1) and torch.equal(v0, v1) and torch.equal(w0, w1)
+    assert s1["iters_run"] == s0["iters_run"]
+    # the same state; the partial sums of its residual group the pixels per strip of the kernel
+    # that ran the last iteration (pinned 2-row strips against the built-in height)
+    assert s1["residual"] == pytest.approx(s0["residual"], rel=1e-6, abs=1e-12)
+    if stop == "never":
+        assert s0["iters_run"] == 2 * iters
+        u2, v2, _, _ = _solve(ctx, pr, rows_per_warp=0, **kw)
+        assert torch.equal(u1, u2) and torch.equal(v1, v2)
+    else:
+        assert s0["iters_run"] < 2 * iters
+
+
+def test_stopping_rule_launch_counts(ctx):
+    """Forty iterations with the stopping test: 16 iteration launches on the tile path against 40
+    with a pinned strip height (each with the same four checks)."""
+    P = flow.default_params(lam=5.0, levels=1, warps=1, iters=40, engine=flow.OF_ENGINE_STREAM, tol=1e-30)
+    n_tile = flow.of_solve_kernel_count(ctx, 480, 640, P)
+    P.rows_per_warp = 2
+    n_rows = flow.of_solve_kernel_count(ctx, 480, 640, P)
+    assert n_rows - n_tile == 40 - 16
