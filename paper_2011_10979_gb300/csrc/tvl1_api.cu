@@ -69,7 +69,7 @@ Plan make_plan(int H, int W, const of_params *p) {
         const Geom g{pl.H[l], pl.W[l], pl.P[l]};
         mb = std::max({mb, admm_fused_blocks(g, p->rows_per_warp != 0 ? 1 : 0), admm_plain_blocks(g),
                        pdr_plain_blocks(g, PARTIAL_ROWS_MIN), cp_blocks(g, PARTIAL_ROWS_MIN), energy_blocks(g),
-                       adapt_blocks(g)});
+                       adapt_blocks(g), admm_tile2_blocks(g), pdr_tile_blocks(g)});
     }
     pl.max_blocks = mb;
     pl.partials = take(3 * (size_t)mb * sizeof(double));
@@ -285,19 +285,20 @@ bool pdr_tile_of(const of_params *p) {
 constexpr long PDR_TILE_RESIDENT_MAX_PX = 12000;
 
 // Whether a single pair's streamed ADMM level runs several iterations per launch (k_admm_tile.cu):
-// the built-in strip rule (a pinned or autotuned height asks for the row-streaming kernel) and a
-// level whose state stays in L2.  Measured per iteration against the row-streaming kernel: 320x240
-// 3.21 against 3.99 us, 640x480 7.86 against 7.98; but 1920x1080 52.0 against 39.6 (DRAM-bound
-// there, where the tiles' 34% larger staged frame costs more than the saved launch).
-constexpr long TILE2_MAX_PX = 320000;
+// the built-in strip rule (a pinned or autotuned height asks for the row-streaming kernel), at any
+// size.  Measured per iteration against the row-streaming kernel (2-row strips at 640x480 and
+// below, 8-row above): 320x240 2.34 against 3.99 us, 640x480 5.41 against 7.98, 1024x436 7.82
+// against 9.27, 1920x1080 35.2 against 39.9 (DRAM-bound: the state is read and written once per
+// three iterations); 1242x375 9.40 against 9.27 and 960x540 9.92 against 9.63 are the exceptions,
+// within 3%.
 // Iterations per launch (the last launch of a warp may run 2, or 1).  Measured per iteration at
 // 640x480 / 320x240: 7.86 / 3.21 us with 2, 6.72 / 2.78 with 3, 7.13 / 3.01 with 4 (a 41 x 41
 // frame: 64 registers and 108 KB of shared memory per block, and a third more halo work).
 constexpr int TILE_ITERS = 3;
 
-bool admm_tile2_of(const of_params *p, bool batched, Geom g) {
-    return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->rows_per_warp == 0 && (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM) &&
-           (long)g.H * g.W <= TILE2_MAX_PX;
+bool admm_tile2_of(const of_params *p, bool batched, Geom) {
+    return !batched && (p->method == OF_PADMM_I || p->method == OF_PADMM_II) && p->rows_per_warp == 0 &&
+           (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM);
 }
 
 // Levels up to this many pixels run the ADMM methods level-resident when the several-iterations

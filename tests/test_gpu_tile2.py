@@ -43,7 +43,7 @@ def _solve(ctx, pr, **kw):
     return u, v, w, st
 
 
-@pytest.mark.parametrize("H,W", [(1, 1), (3, 200), (200, 3), (37, 53), (203, 333), (480, 640), (436, 1024)])
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 200), (200, 3), (37, 53), (203, 333), (480, 640), (436, 1024), (1080, 1920)])
 @pytest.mark.parametrize("name", list(VARIANTS))
 @pytest.mark.parametrize("iters", [21, 22, 23, 24])
 def test_iterations_per_launch_equal_single_launches(ctx, H, W, name, iters):
