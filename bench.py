@@ -190,9 +190,9 @@ def run_level(args):
     """Single-level solves for a profiler: the 40x30 and 640x480 levels of the bench pair's kind
     (one warp, 30 inner iterations, three solves each) of --method (pADMM unless set) on the given
     engine, strip height --rows-per-warp (ADMM only; unset: the built-in rule, which on the
-    streaming engine runs these levels two iterations per launch).  A 40x30 level runs a handful of
-    warps, each walking its strip alone on its SM, so it shows the latency of one warp's row steps;
-    with --method pdr the 640x480 level runs the one-launch pDR tile kernel."""
+    streaming engine runs these levels three iterations per launch on the tile kernel, as ALG1
+    does).  A pinned height runs the row-streaming kernel, whose 40x30 level shows the latency of
+    one warp's row steps; with --method pdr the 640x480 level runs the one-launch pDR tile kernel."""
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)

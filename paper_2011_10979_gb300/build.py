@@ -14,9 +14,9 @@ OBJ = os.path.join(PKG, "_build")
 SOURCES = ["tvl1_api.cu", "tvl1_serve.cu", "tvl1_step.cu", "tvl1_noalloc.cu", "k_pyramid.cu", "k_admm.cu", "k_admm_roll.cu", "k_admm_roll_f32.cu",
            "k_admm_roll_f16.cu", "k_admm_roll_bf16.cu", "k_admm_persist.cu", "k_admm_persist_f32.cu",
            "k_admm_persist_f16.cu", "k_admm_persist_bf16.cu", "k_resident.cu", "k_pdr.cu", "k_cp.cu",
-           "k_reduce.cu", "k_probe.cu", "k_adapt.cu", "k_admm_tile.cu"]
+           "k_reduce.cu", "k_probe.cu", "k_adapt.cu", "k_admm_tile.cu", "k_cp_tile.cu"]
 HEADERS = ["tvl1_internal.h", "tvl1_device.cuh", "k_admm_roll.cuh", "k_admm_math.cuh", "k_pdr_math.cuh",
-           "k_cp_math.cuh", "k_admm_persist.cuh", "tvl1_plan.h", "tvl1_step.h"]
+           "k_cp_math.cuh", "k_tile_cells.cuh", "k_admm_persist.cuh", "tvl1_plan.h", "tvl1_step.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

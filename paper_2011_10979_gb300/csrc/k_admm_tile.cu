@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "k_admm_math.cuh"
+#include "k_tile_cells.cuh"
 #include "tvl1_device.cuh"
 
 namespace tvl1 {
@@ -84,45 +85,10 @@ __global__ void __launch_bounds__(Shape<TT, NI>::NT) k_admm_tile2(IterArgs A) {
     }
     const StepK K = step_coefs(A.k, a_tilde_of(A.k, A.ms_max), c_of(A.k, A.ms_max));
     __syncthreads();
-    // the in-image cells of the square of offsets [LO, HI] (compile-time bounds, n >= TT a side).
-    // 32 consecutive cells of the square would straddle two of its rows, FS - n floats apart, and
-    // most warps would meet a two-way bank conflict on every shared-memory access.  Instead:
-    //  - 16-pixel tiles (FS = 21 or 23): lane t of the run covers frame offset t from the square's
-    //    first cell, rows counted at the frame pitch, so a warp's addresses are consecutive; the
-    //    FS - n cells past each row's end idle their lanes (over a 22-cell square with FS = 23,
-    //    16 wavefronts per access to a plane against 31);
-    //  - 32-pixel tiles: a warp task is a whole row of the square's first 32 columns (consecutive
-    //    addresses) or a run of 32 cells of its remaining n - 32 columns, row by row (at most
-    //    two-way conflicts there).  Measured per iteration at 640x480: 6.72 us with consecutive
-    //    cells of the square, 5.48 pitch-wrapped, 5.41 with row tasks.
-    // The east, west, north and south neighbours of the cells a warp touches fall in the same
-    // number of banks as the cells themselves.
+    // the in-image cells of the square of offsets [LO, HI], dealt to the threads conflict-free
+    // (k_tile_cells.cuh)
     auto for_cells = [&](auto LO_, auto HI_, auto &&f) {
-        constexpr int lo = decltype(LO_)::value, n = decltype(HI_)::value - lo + 1, x0 = (lo + OFF) * (FS + 1);
-        static_assert(n >= TT, "square narrower than a tile");
-        if constexpr (TT == 16) {
-            for (int t = threadIdx.x; t < (n - 1) * FS + n; t += NT) {
-                const int r = t / FS, c = t % FS;
-                const int i = fi + lo + OFF + r, j = fj + lo + OFF + c;
-                if (c < n && i >= 0 && i < H && j >= 0 && j < W) f(x0 + t, i, j);
-            }
-        } else {
-            constexpr int M = n - TT, NTASK = n + (n * M + 31) / 32;
-            const int lane = threadIdx.x & 31;
-            for (int task = threadIdx.x >> 5; task < NTASK; task += NT / 32) {
-                int r = task, c = lane;
-                if constexpr (M > 0) {
-                    if (task >= n) {
-                        const int q = (task - n) * 32 + lane;
-                        if (q >= n * M) continue;
-                        r = q / M;
-                        c = TT + q % M;
-                    }
-                }
-                const int i = fi + lo + OFF + r, j = fj + lo + OFF + c;
-                if (i >= 0 && i < H && j >= 0 && j < W) f(x0 + r * FS + c, i, j);
-            }
-        }
+        tile_cells<TT, FS, OFF, NT, decltype(LO_)::value, decltype(HI_)::value>(fi, fj, H, W, f);
     };
     // y as the streaming kernel reads it: the stored value, rounded to the storage type
     auto Y = [&](int k, int x) { return storage_round<T>(S(SY0 + k)[x]); };

@@ -69,7 +69,7 @@ Plan make_plan(int H, int W, const of_params *p) {
         const Geom g{pl.H[l], pl.W[l], pl.P[l]};
         mb = std::max({mb, admm_fused_blocks(g, p->rows_per_warp != 0 ? 1 : 0), admm_plain_blocks(g),
                        pdr_plain_blocks(g, PARTIAL_ROWS_MIN), cp_blocks(g, PARTIAL_ROWS_MIN), energy_blocks(g),
-                       adapt_blocks(g), admm_tile2_blocks(g), pdr_tile_blocks(g)});
+                       adapt_blocks(g), admm_tile2_blocks(g), pdr_tile_blocks(g), cp_tile_blocks(g)});
     }
     pl.max_blocks = mb;
     pl.partials = take(3 * (size_t)mb * sizeof(double));
@@ -301,6 +301,18 @@ bool admm_tile2_of(const of_params *p, bool batched, Geom) {
            (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM);
 }
 
+// Whether a single pair's streamed ALG1 level runs several iterations per launch (k_cp_tile.cu):
+// the built-in block height (a pinned or autotuned one asks for the one-iteration kernel k_cp).
+bool cp_tile_of(const of_params *p, bool batched) {
+    return !batched && p->method == OF_CP && p->rows_per_warp == 0 &&
+           (p->engine == OF_ENGINE_FUSED || p->engine == OF_ENGINE_STREAM);
+}
+
+// Levels up to this many pixels run ALG1 level-resident when its tile kernel is the alternative
+// (measured per iteration, resident against tile kernel: 1.03 / 1.21 us at 40x30, 1.21 / 1.29 at
+// 80x60, 1.79 / 1.29 at 120x90, 2.41 / 1.32 at 160x120).
+constexpr long CP_TILE_RESIDENT_MAX_PX = 6000;
+
 // Levels up to this many pixels run the ADMM methods level-resident when the several-iterations
 // tile kernel is the alternative (measured per iteration, resident against tile kernel: 1.04 /
 // 1.51 us at 40x30, 1.34 / 1.58 at 80x60, 1.93 / 1.58 at 120x90, 2.67 / 1.61 at 160x120); against
@@ -313,6 +325,7 @@ bool use_resident(const of_params *p, Geom g, bool batched = false) {
     if (p->engine != OF_ENGINE_FUSED && p->engine != OF_ENGINE_PERSISTENT) return false;
     if (pdr_tile_of(p)) return (long)g.H * g.W <= PDR_TILE_RESIDENT_MAX_PX;
     if (admm_tile2_of(p, batched, g)) return (long)g.H * g.W <= TILE_RESIDENT_MAX_PX;
+    if (cp_tile_of(p, batched)) return (long)g.H * g.W <= CP_TILE_RESIDENT_MAX_PX;
     return admm_resident_preferred(g, p->method);
 }
 
@@ -895,13 +908,14 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
             // pairs left for one launch per iteration: the tile work-list (ADMM), all pairs (pDR),
             // the non-resident pairs (ALG1)
             const bool streamed = !persl && (batched ? ((cp || pdr) ? B.nres[l] < n : B.ntiles[l] > 0) : !res1);
-            // single pair, ADMM, the built-in strip rule: several iterations per launch.  With the
+            // single pair, ADMM or ALG1, the built-in strip rule or block height: several iterations
+            // per launch (k_admm_tile.cu, k_cp_tile.cu).  With the
             // stopping test every ten iterations run as launches of 3, 3, 3 and 1: the tested state
             // is a single-iteration launch's (its residual partials), an even number of launches
             // leaves it in bufs[start2] as on the one-launch-per-iteration path, and the warp's last
             // launch is a single iteration too, so the final residual sums the same partials
             // whether or not the test stopped the warp.
-            const bool tile2 = streamed && admm_tile2_of(p, batched, geom_of(*pc[0].pl, l));
+            const bool tile2 = streamed && (admm_tile2_of(p, batched, geom_of(*pc[0].pl, l)) || cp_tile_of(p, batched));
             int par = start2, last_nb = 0;  // the several-iterations path's buffer parity and last block count
             for (int it = 0, step = 1; streamed && it < rest; it += step) {
                 step = 1;
@@ -938,7 +952,13 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         if (plain) launch_pdr_plain(a, s);
                         else launch_pdr_fused(a, prec, pflow, s);
                     } else if (cp) {
-                        launch_cp(a, prec, pflow, s);
+                        if (step > 1) {
+                            launch_cp_tile(a, step, prec, pflow, s);
+                            last_nb = cp_tile_blocks(g);
+                        } else {
+                            launch_cp(a, prec, pflow, s);
+                            last_nb = blocks_of(g, l);
+                        }
                     } else if (step > 1) {
                         launch_admm_tile2(a, step, prec, pflow, s);
                         last_nb = admm_tile2_blocks(g);
@@ -948,7 +968,7 @@ void enqueue_solve(of_ctx *ctx, const Batch &B, const of_params *p, cudaStream_t
                         last_nb = blocks_of(g, l);
                     }
                     if (check) {
-                        const int nb = step > 1 ? admm_tile2_blocks(g) : blocks_of(g, l);
+                        const int nb = step > 1 ? (cp ? cp_tile_blocks(g) : admm_tile2_blocks(g)) : blocks_of(g, l);
                         const double rows = (double)g.H * g.W * (has_w ? 3.0 : 2.0);
                         launch_reduce_check(c.partials, nb, &c.misc->res_check, rows, p->tol, &c.misc->done,
                                             &c.misc->iters, 10, s);

@@ -240,14 +240,17 @@ void launch_count_iters_batched(const PairScalars *ps, int npairs, int n, bool u
 void launch_parity_fix(const Fields &from, const Fields &to, Geom g, int prec, int prec_flow, const int *done,
                        int want_done, cudaStream_t s);
 
-// ---------------------------------------------------------------- several ADMM iterations per launch (k_admm_tile.cu)
-// Single pair, fixed schedule: ni (2 or 3) consecutive iterations of the fused ADMM engine in one
-// launch over TT x TT tiles (admm_tile2_size: 32, or 16 on small levels), reading a.in and writing
-// a.out, bitwise ni launches of the streaming kernel; partials (of the last iteration) in
-// admm_tile2_blocks(a.g) slots.
+// ---------------------------------------------------------------- several iterations per launch (k_admm_tile.cu, k_cp_tile.cu)
+// Single pair: ni (2 or 3) consecutive iterations of the fused ADMM engine (ALG1: of k_cp) in one
+// launch over TT x TT tiles (*_tile_size: 32, or 16 on small levels), reading a.in and writing
+// a.out, bitwise ni launches of the one-iteration kernel; partials (of the last iteration) in
+// *_tile_blocks(a.g) slots.
 int admm_tile2_size(Geom g);
 int admm_tile2_blocks(Geom g);
 void launch_admm_tile2(const IterArgs &a, int ni, int prec, int prec_flow, cudaStream_t s);
+int cp_tile_size(Geom g);
+int cp_tile_blocks(Geom g);
+void launch_cp_tile(const IterArgs &a, int ni, int prec, int prec_flow, cudaStream_t s);
 
 // ---------------------------------------------------------------- adaptive ADMM step (k_adapt.cu)
 // Residual balancing of c after one ADMM iteration prev -> cur (both state buffers intact): the

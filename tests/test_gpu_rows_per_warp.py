@@ -128,11 +128,13 @@ def test_autotuned_single_pair(ctx):
 
 
 def test_rows_report_for_other_kernels(ctx):
-    """ALG1 and pDR with two sweeps report the block height of their per-iteration kernels on the
-    levels they stream (8 by default) and 0 on the level-resident one; pDR with one sweep (its
-    one-launch tile kernel), the plain engine and levels below out_level report 0."""
-    for kw in (dict(method=flow.OF_PDR, gs_sweeps=2), dict(method=flow.OF_CP)):
-        assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, **kw)) == [8, 8, 0]
+    """ALG1 and pDR with two sweeps report the block height of their one-iteration kernels on the
+    levels they stream (8 by default) and 0 on the level-resident one (pDR: 160x120; ALG1 streams
+    it, its tile kernel being faster there); pDR with one sweep (its one-launch tile kernel), the
+    plain engine and levels below out_level report 0."""
+    pdr2 = flow.default_params(levels=3, method=flow.OF_PDR, gs_sweeps=2)
+    assert flow.of_rows_per_warp(ctx, [(480, 640)], pdr2) == [8, 8, 0]
+    assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, method=flow.OF_CP)) == [8, 8, 8]
     assert flow.of_rows_per_warp(ctx, [(480, 640)], flow.default_params(levels=3, method=flow.OF_PDR)) == [0, 0, 0]
     plain = flow.default_params(levels=3, engine=flow.OF_ENGINE_PLAIN)
     assert flow.of_rows_per_warp(ctx, [(480, 640)], plain) == [0, 0, 0]
