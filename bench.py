@@ -181,7 +181,7 @@ def run_batch16(args):
     from paper_2011_10979_gb300 import flow
     from paper_2011_10979_gb300.build import build
     build()
-    r = batch_measure(flow, torch, dev, n=16, distinct=16, fp32_flow=1, steps=1, engine=flow.OF_ENGINE_STREAM,
+    r = batch_measure(flow, torch, dev, n=16, fp32_flow=1, steps=1, engine=flow.OF_ENGINE_STREAM,
                       rows_per_warp=args.rows_per_warp)
     print(json.dumps({"legs": "batch16", "batch": r}))
 
@@ -358,18 +358,27 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, steps=2, engine=None,
-                  rows_per_warp=-1):
-    """Uneven-size batch: n pairs with sizes drawn uniformly from {96x64, 320x240, 640x480,
-    1024x436, 1242x375}, affine+box motion up to 15 px (`distinct` seeded pairs, each used
-    n/distinct times), BF16 storage, FP32 last warp, 5 levels x 10 warps x 100 iterations, solved
-    with of_solve_batch (one work-list launch per inner iteration for all pairs).  The streaming
-    kernel's strip height is autotuned per level on the (untimed) first solve unless rows_per_warp
-    sets it."""
-    from paper_2011_10979_gb300 import synth
+_BATCH_PAIRS = {}
+
+
+def batch_pairs(n):
+    """The n distinct seeded pairs of the uneven-size batch, rendered once per process on the host
+    threads (spawned workers; input generation only)."""
+    if n not in _BATCH_PAIRS:
+        from paper_2011_10979_gb300 import synth
+        ranks = max(1, int(os.environ.get("LOCAL_WORLD_SIZE", os.environ.get("WORLD_SIZE", "1"))))
+        _BATCH_PAIRS[n] = synth.batch_pairs(n=n, workers=max(1, min(16, (os.cpu_count() or 1) // ranks)))
+    return _BATCH_PAIRS[n]
+
+
+def batch_measure(flow, torch, dev, n=256, prec=None, fp32_flow=1, steps=2, engine=None, rows_per_warp=-1):
+    """Uneven-size batch: n distinct pairs, each with its own seed, sizes drawn uniformly from
+    {96x64, 320x240, 640x480, 1024x436, 1242x375}, affine+box motion up to 15 px, BF16 storage,
+    FP32 last warp, 5 levels x 10 warps x 100 iterations, solved with of_solve_batch (one
+    work-list launch per inner iteration for all pairs).  The streaming kernel's strip height is
+    autotuned per level on the (untimed) first solve unless rows_per_warp sets it."""
     prec = flow.OF_PREC_BF16 if prec is None else prec
-    base = synth.batch_pairs(n=distinct)
-    pairs = [base[k % distinct] for k in range(n)]
+    pairs = batch_pairs(n)
     I0 = [torch.from_numpy(p.I0).to(dev) for p in pairs]
     I1 = [torch.from_numpy(p.I1).to(dev) for p in pairs]
     P = flow.default_params(method=flow.OF_PADMM_I, lam=LAM, beta=BETA, levels=LEVELS, warps=WARPS, iters=ITERS,
@@ -390,7 +399,7 @@ def batch_measure(flow, torch, dev, n=256, distinct=32, prec=None, fp32_flow=1, 
     bpp = 92.0 if prec == flow.OF_PREC_FP32 else (58.0 if fp32_flow else 46.0)
     name = {0: "fp32", 1: "fp16", 2: "bf16"}[prec] + ("" if prec == flow.OF_PREC_FP32 else
                                                         ("_duals+fp32_flow" if fp32_flow else "_all"))
-    return {"workload": "%d pairs uneven sizes (%d distinct seeded pairs), pADMM, 5x10x100" % (n, distinct),
+    return {"workload": "%d distinct seeded pairs of uneven sizes, pADMM, 5x10x100" % n,
             "storage": name, "value": n / t, "unit": "flows/s",
             "rows_per_warp": {"mode": "autotuned" if P.rows_per_warp == -1 else "set", "per_level": rows},
             "s_per_batch": t, "gpix_iter_per_s": work / 1e3 / t,

@@ -137,13 +137,17 @@ def affine_rect_pair(H=480, W=640, seed=1, sigma=0.01, rot_deg=2.0, zoom=1.03, s
     bx, by = rect_pos
     mx, my = rect_motion
     in0 = (x >= bx) & (x < bx + rw) & (y >= by) & (y < by + rh)
-    f0 = np.where(in0, 1.5 * fg(x - bx, y - by), bg(x, y))
+    # the box texture is evaluated on the box's pixels only (the textures are pointwise, so the
+    # values are those of a whole-image evaluation)
+    f0 = bg(x, y)
+    f0[in0] = 1.5 * fg(x[in0] - bx, y[in0] - by)
     # frame 1: inverse affine for the background; the box moved by (mx, my)
     Ai = np.linalg.inv(A)
     px, py = x - cx - t[0], y - cy - t[1]
     sx, sy = Ai[0, 0] * px + Ai[0, 1] * py + cx, Ai[1, 0] * px + Ai[1, 1] * py + cy
     in1 = (x >= bx + mx) & (x < bx + mx + rw) & (y >= by + my) & (y < by + my + rh)
-    f1 = np.where(in1, 1.5 * fg(x - bx - mx, y - by - my), bg(sx, sy))
+    f1 = bg(sx, sy)
+    f1[in1] = 1.5 * fg(x[in1] - bx - mx, y[in1] - by - my)
     # ground truth of frame-0 pixels
     ax = A[0, 0] * (x - cx) + A[0, 1] * (y - cy) + cx + t[0] - x
     ay = A[1, 0] * (x - cx) + A[1, 1] * (y - cy) + cy + t[1] - y
@@ -187,15 +191,33 @@ def layered_pair(H=436, W=1024, seed=2, sigma=0.02, n_layers=6, max_shift=20.0, 
 BATCH_SIZES = ((64, 96), (240, 320), (480, 640), (436, 1024), (375, 1242))   # (H, W)
 
 
-def batch_pairs(n=256, seed=3, max_motion=15.0):
-    """Uneven-size batch: sizes drawn uniformly from BATCH_SIZES, each pair an affine+box pair
-    with its own seed (random_affine_rect_pair)."""
+def batch_specs(n=256, seed=3):
+    """(H, W, pair seed) of each pair of the uneven-size batch, sizes drawn uniformly from
+    BATCH_SIZES.  The first k specs of a batch of n are those of a batch of k."""
     rng = np.random.default_rng(seed)
     out = []
-    for k in range(n):
+    for _ in range(n):
         H, W = BATCH_SIZES[int(rng.integers(0, len(BATCH_SIZES)))]
-        out.append(random_affine_rect_pair(H, W, int(rng.integers(0, 2**31 - 1)), max_motion))
+        out.append((H, W, int(rng.integers(0, 2**31 - 1))))
     return out
+
+
+def _spec_pair(spec, max_motion):
+    H, W, s = spec
+    return random_affine_rect_pair(H, W, s, max_motion)
+
+
+def batch_pairs(n=256, seed=3, max_motion=15.0, workers=1):
+    """Uneven-size batch: one affine+box pair (random_affine_rect_pair) with its own seed per
+    spec of batch_specs.  workers > 1 renders the pairs in that many spawned processes (the
+    pairs are the same)."""
+    specs = batch_specs(n, seed)
+    if workers <= 1 or n <= 1:
+        return [_spec_pair(sp, max_motion) for sp in specs]
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max_workers=min(workers, n), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_spec_pair, specs, [max_motion] * n, chunksize=4))
 
 
 def random_affine_rect_pair(H, W, seed, max_motion=15.0, sigma=0.01):

@@ -72,6 +72,16 @@ def test_batch_sizes_and_motion(n):
         assert d.max() <= 15.0 + 0.05 * np.hypot(W / 2.0, H / 2.0) + 1e-6
 
 
+def test_batch_pairs_in_workers_equal_serial_and_extend_shorter_batches():
+    serial = synth.batch_pairs(n=6)
+    pooled = synth.batch_pairs(n=6, workers=2)
+    assert [sp[:2] for sp in synth.batch_specs(6)] == [p.I0.shape for p in serial]
+    assert synth.batch_specs(4) == synth.batch_specs(6)[:4]
+    for a, b in zip(serial, pooled):
+        for k in ("I0", "I1", "u_true", "v_true"):
+            assert np.array_equal(getattr(a, k), getattr(b, k))
+
+
 def test_serving_mix_and_arrivals():
     sizes = synth.serve_sizes(2000)
     frac = {s: sizes.count(s) / len(sizes) for s, _ in synth.SERVE_MIX}
