@@ -36,31 +36,33 @@ __device__ __forceinline__ float bilinear(const T *f, int H, int W, int P, float
     return (1.f - fy) * top + fy * bot;
 }
 
-// Sample position j + d clamped to [0, n-1], as integer part and fraction.  The fraction is taken
-// from d itself, so it keeps d's full precision however large j is.
-__device__ __forceinline__ void split_pos(int j, float d, int n, int &x0, float &fx) {
-    const float xs = (float)j + d;
-    if (!(xs > 0.f)) {              // also catches NaN
+// Sample position j + d clamped to [0, n-1], as integer part and fraction, in FP64: j + d and
+// its fraction are exact there for any FP32 displacement d.
+__device__ __forceinline__ void split_pos_f64(int j, float d, int n, int &x0, double &fx) {
+    const double xs = (double)j + (double)d;
+    if (!(xs > 0.0)) {              // also catches NaN
         x0 = 0;
-        fx = 0.f;
-    } else if (xs >= (float)(n - 1)) {
+        fx = 0.0;
+    } else if (xs >= (double)(n - 1)) {
         x0 = n - 1;
-        fx = 0.f;
+        fx = 0.0;
     } else {
-        const float fl = floorf(d);
-        x0 = min(max(j + (int)fl, 0), n - 1);
-        fx = d - fl;
+        const double fl = floor(xs);
+        x0 = (int)fl;
+        fx = xs - fl;
     }
 }
 
-template <typename T>
-__device__ __forceinline__ float bilinear_split(const T *f, int H, int W, int P, int x0, float fx, int y0, float fy) {
+// Bilinear value of an FP32 plane (H x W, pitch P) at (x0 + fx, y0 + fy) in FP64 arithmetic (the
+// four samples are exact in FP64).
+__device__ __forceinline__ double bilinear_split_f64(const float *f, int H, int W, int P, int x0, double fx, int y0,
+                                                     double fy) {
     const int x1 = min(x0 + 1, W - 1), y1 = min(y0 + 1, H - 1);
-    const float a = Store<T>::ld(f + (size_t)y0 * P + x0), b = Store<T>::ld(f + (size_t)y0 * P + x1);
-    const float c = Store<T>::ld(f + (size_t)y1 * P + x0), d = Store<T>::ld(f + (size_t)y1 * P + x1);
-    const float top = (1.f - fx) * a + fx * b;
-    const float bot = (1.f - fx) * c + fx * d;
-    return (1.f - fy) * top + fy * bot;
+    const double a = __ldg(f + (size_t)y0 * P + x0), b = __ldg(f + (size_t)y0 * P + x1);
+    const double c = __ldg(f + (size_t)y1 * P + x0), d = __ldg(f + (size_t)y1 * P + x1);
+    const double top = (1.0 - fx) * a + fx * b;
+    const double bot = (1.0 - fx) * c + fx * d;
+    return (1.0 - fy) * top + fy * bot;
 }
 
 // Separable Gaussian, first along rows (x), then along columns (y); half-sample symmetric border.
@@ -115,6 +117,10 @@ __global__ void k_derivatives(const float *__restrict__ I, Geom g, float *__rest
 // Warp I1 and its derivatives to (x + u0, y + v0) (clamped), linearise around d0:
 // It = I1w - I0 - Ix u0 - Iy v0, so that rho(w, d) = Ix u + Iy v + beta w + It.
 // The block max of M_s = beta^2 + Ix^2 + Iy^2 (of the stored, rounded values) raises *ms_max.
+// The interpolation and It run in FP64 and are rounded once, when stored: It is a small difference
+// of terms up to |grad I| |d0|, and the L1 data term puts the flow of weakly textured pixels on the
+// line Ix u + Iy v + It = 0, so an FP32 It moved those pixels by up to a few 1e-3 px over a whole
+// schedule (measured against the FP64 oracle).  The kernel runs once per warp; FP64 costs little.
 template <typename T, typename TF>
 __global__ void k_warp(const float *__restrict__ I0, const float *__restrict__ I1, const float *__restrict__ I1x,
                        const float *__restrict__ I1y, const TF *__restrict__ u0, const TF *__restrict__ v0, Geom g,
@@ -126,15 +132,15 @@ __global__ void k_warp(const float *__restrict__ I0, const float *__restrict__ I
         const size_t o = (size_t)i * g.pitch + j;
         const float uu = Store<TF>::ld(u0 + o), vv = Store<TF>::ld(v0 + o);
         int x0, y0;
-        float fx, fy;
-        split_pos(j, uu, g.W, x0, fx);
-        split_pos(i, vv, g.H, y0, fy);
-        const float w1 = bilinear_split<float>(I1, g.H, g.W, g.pitch, x0, fx, y0, fy);
-        const float gx = bilinear_split<float>(I1x, g.H, g.W, g.pitch, x0, fx, y0, fy);
-        const float gy = bilinear_split<float>(I1y, g.H, g.W, g.pitch, x0, fx, y0, fy);
-        Store<T>::st(Ix + o, gx);
-        Store<T>::st(Iy + o, gy);
-        Store<T>::st(It + o, w1 - __ldg(I0 + o) - gx * uu - gy * vv);
+        double fx, fy;
+        split_pos_f64(j, uu, g.W, x0, fx);
+        split_pos_f64(i, vv, g.H, y0, fy);
+        const double w1 = bilinear_split_f64(I1, g.H, g.W, g.pitch, x0, fx, y0, fy);
+        const double gx = bilinear_split_f64(I1x, g.H, g.W, g.pitch, x0, fx, y0, fy);
+        const double gy = bilinear_split_f64(I1y, g.H, g.W, g.pitch, x0, fx, y0, fy);
+        Store<T>::st(Ix + o, (float)gx);
+        Store<T>::st(Iy + o, (float)gy);
+        Store<T>::st(It + o, (float)(w1 - (double)__ldg(I0 + o) - gx * (double)uu - gy * (double)vv));
         const float gxr = Store<T>::ld(Ix + o), gyr = Store<T>::ld(Iy + o);
         ms = beta * beta + gxr * gxr + gyr * gyr;
     }

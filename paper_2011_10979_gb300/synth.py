@@ -216,8 +216,13 @@ def batch_pairs(n=256, seed=3, max_motion=15.0, workers=1):
         return [_spec_pair(sp, max_motion) for sp in specs]
     import concurrent.futures as cf
     import multiprocessing as mp
-    with cf.ProcessPoolExecutor(max_workers=min(workers, n), mp_context=mp.get_context("spawn")) as ex:
-        return list(ex.map(_spec_pair, specs, [max_motion] * n, chunksize=4))
+    try:
+        with cf.ProcessPoolExecutor(max_workers=min(workers, n), mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_spec_pair, specs, [max_motion] * n, chunksize=4))
+    except (OSError, cf.process.BrokenProcessPool):
+        # no process pool on this host (e.g. no POSIX semaphores): threads give the same pairs
+        with cf.ThreadPoolExecutor(max_workers=min(workers, n)) as ex:
+            return list(ex.map(_spec_pair, specs, [max_motion] * n))
 
 
 def random_affine_rect_pair(H, W, seed, max_motion=15.0, sigma=0.01):

@@ -70,8 +70,10 @@ def test_derivatives_and_warp(ctx, orc, H, W):
     assert np.max(np.abs(np64(gx) - rx)) < 1e-6 and np.max(np.abs(np64(gy) - ry)) < 1e-6
     Ix, Iy, It, ms = flow.of_warp_linearise(cu(I0), cu(I1), gx, gy, cu(u0), cu(v0), 0.05)
     Rx, Ry, Rt, rms = orc.warp_linearise(I0, I1, np64(gx), np64(gy), u0, v0, 0.05)
+    # the warp interpolates and forms It in FP64 and rounds once when storing: half an FP32 ulp of
+    # |It| <= 1 + 2 * 0.5 * 5 = 6 is 2.4e-7
     for a, b in ((Ix, Rx), (Iy, Ry), (It, Rt)):
-        assert np.max(np.abs(np64(a) - b)) < 2e-5
+        assert np.max(np.abs(np64(a) - b)) < 1e-6
     assert abs(float(ms.item()) - rms) <= 1e-5 * rms
 
 

@@ -85,13 +85,15 @@ def _errors(u, v, ru, rv):
     return float(np.abs(u - ru).max()), float(np.abs(v - rv).max()), float(np.hypot(u - ru, v - rv).mean())
 
 
-# Measured misses of the max |d| <= 1e-3 px bar after the longest schedules (5,000-9,000 inner
-# iterations in FP32 against FP64): a handful of pixels drift past 1e-3 px while the mean
-# end-point error stays 100-10,000 times below its 1e-2 px bar.  Recorded as failing, not widened.
+# Measured misses of the max |d| <= 1e-3 px bar after the longest schedules (5,000 inner
+# iterations in FP32 against FP64): one to a few pixels drift past 1e-3 px while the mean
+# end-point error stays 200-500 times below its 1e-2 px bar.  Recorded as failing, not widened.
+# An FP32 build of the oracle itself misses these bars by more (pDR 5.0e-3, ALG1 3.4e-3 px), and
+# FP32 storage of the pyramid images alone (FP64 arithmetic everywhere else) already moves single
+# pixels of the ALG1 case by 2.2e-3 px.
 MAX_BAR_MISS = {
-    "pdr_l0": "max|dv| 1.14e-3 px (EPE 5.7e-5 px)",
-    "alg1_l0": "max|du| 2.42e-3 px, max|dv| 1.80e-3 px (EPE 2.0e-5 px)",
-    "layered_fp32": "max|dv| 1.33e-3 px (EPE 8.1e-7 px)",
+    "pdr_l0": "max|dv| 1.15e-3 px (EPE 5.7e-5 px)",
+    "alg1_l0": "max|du| 2.52e-3 px, max|dv| 1.11e-3 px (EPE 1.9e-5 px)",
 }
 
 
@@ -115,11 +117,9 @@ def test_pdr_and_alg1_schedules_at_640x480(ctx, ref, name, request):
 
 @pytest.mark.parametrize("prec,fp32_flow", [(flow.OF_PREC_FP32, 1), (flow.OF_PREC_FP16, 1), (flow.OF_PREC_BF16, 1),
                                             (flow.OF_PREC_FP16, 0), (flow.OF_PREC_BF16, 0)])
-def test_layered_1024x436_full_schedule(ctx, ref, prec, fp32_flow, request):
+def test_layered_1024x436_full_schedule(ctx, ref, prec, fp32_flow):
     """The precision workload at its own schedule (6 levels, 10 warps, 150 iterations).  FP32 and
     16-bit duals/data with FP32 flow fields meet the EPE bar; all-16-bit storage is reported only."""
-    if prec == flow.OF_PREC_FP32:
-        _expect_max_bar_miss(request, "layered_fp32")
     pair = jobs()["layered"][0]
     P = flow.default_params(precision=prec, fp32_last_warp=1, fp32_flow=fp32_flow, **LAYERED)
     u, v, _, _ = flow.of_solve(ctx, cu(pair.I0), cu(pair.I1), P)
