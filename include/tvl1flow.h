@@ -35,6 +35,10 @@ extern "C" {
 
 typedef struct of_ctx of_ctx;
 
+/* Largest image side the whole-solve entry points and the serving loop accept (H and W each); the
+ * kernels' grids and the arena's offsets are sized for it. */
+#define OF_MAX_SIDE 32768
+
 typedef enum {
     OF_OK = 0,
     OF_EINVAL = 1,    /* invalid argument (sizes, pitches, parameters, NULL pointers) */
@@ -222,7 +226,8 @@ of_status of_persistent_selftest(int H, int W, int iters, int withhold, double w
 of_status of_l2_bandwidth(size_t bytes, int passes, double *gbps);
 
 /* Solves one pair (whole schedule: pyramid, levels, warps, inner iterations; Sec. 3-4).
- * I0, I1: H x W FP32 images (device, pitch `pitch`).  u, v (and w unless NULL): outputs of size
+ * I0, I1: H x W FP32 images (device, pitch `pitch`), 1 <= H, W <= OF_MAX_SIDE (else OF_EINVAL).
+ * u, v (and w unless NULL): outputs of size
  * H_l x W_l at level params->out_level, FP32, pitch `out_pitch` (>= W_l).  stats: optional; if
  * given the call synchronises `stream` and fills it.  The first call for a new (H, W, params)
  * captures a CUDA graph that later calls replay. */

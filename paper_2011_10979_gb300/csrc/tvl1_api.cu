@@ -128,7 +128,8 @@ of_status fail(of_status st, const std::string &msg) {
 
 of_status validate(const of_params *p, int H, int W) {
     if (!p) return fail(OF_EINVAL, "params is NULL");
-    if (H < 1 || W < 1) return fail(OF_EINVAL, "image sizes must be >= 1");
+    if (H < 1 || W < 1 || H > OF_MAX_SIDE || W > OF_MAX_SIDE)
+        return fail(OF_EINVAL, "image sizes must lie in [1, " + std::to_string(OF_MAX_SIDE) + "]");
     if (p->method < 0 || p->method > 3) return fail(OF_EINVAL, "unknown method");
     if (!(p->lambda > 0.f) || !isfinite(p->lambda)) return fail(OF_EINVAL, "lambda must be > 0");
     if (!(p->beta >= 0.f) || !isfinite(p->beta)) return fail(OF_EINVAL, "beta must be >= 0");

@@ -389,8 +389,8 @@ of_status of_server_submit(of_ctx *ctx, const float *I0, const float *I1, int H,
         tvl1_set_error("of_server_submit: no serving loop on this context");
         return OF_EBUSY;
     }
-    if (!I0 || !I1 || !req_id || H < 1 || W < 1) {
-        tvl1_set_error("of_server_submit: bad arguments");
+    if (!I0 || !I1 || !req_id || H < 1 || W < 1 || H > OF_MAX_SIDE || W > OF_MAX_SIDE) {
+        tvl1_set_error("of_server_submit: bad arguments (NULL pointer, or a side outside [1, OF_MAX_SIDE])");
         return OF_EINVAL;
     }
     Request *r = new Request();

@@ -50,6 +50,11 @@ def test_arena_bytes_and_validation_without_gpu(L):
         q = flow.default_params(**{"levels": 5, **bad})
         assert L.of_arena_bytes(480, 640, ctypes.byref(q)) == 0
     assert L.of_arena_bytes(0, 640, ctypes.byref(p)) == 0
+    side = 32768    # OF_MAX_SIDE in include/tvl1flow.h
+    assert L.of_arena_bytes(side, 8, ctypes.byref(p)) > 0 and L.of_arena_bytes(8, side, ctypes.byref(p)) > 0
+    for H, W in ((side + 1, 8), (8, side + 1)):
+        assert L.of_arena_bytes(H, W, ctypes.byref(p)) == 0
+        assert b"[1, 32768]" in L.of_last_error(None)
     st = L.of_solve(None, None, None, 10, 10, 10, ctypes.byref(p), None, None, None, 10, None, None)
     assert st == flow.OF_EINVAL
     assert b"ctx" in L.of_last_error(None)
