@@ -99,8 +99,12 @@ def _grid(H, W):
 
 
 # ------------------------------------------------------------------ workloads
-def sinusoid_pair(H=48, W=64, seed=0, sigma=0.01, left=(1.5, -0.5), right=(-0.75, 1.0)):
-    """64 x 48 case: 16 random sinusoids, piecewise-constant motion (left half / right half)."""
+def sinusoid_pair(H=48, W=64, seed=0, sigma=0.01, left=(1.5, -0.5), right=(-0.75, 1.0), render="analytic"):
+    """64 x 48 case: 16 random sinusoids, piecewise-constant motion (left half / right half).
+
+    render="analytic": both frames evaluate the closed-form texture (frame 1 at y - D(y)), each with
+    its own noise.  render="bilinear": frame 1 is frame 0 itself (noise included) resampled
+    bilinearly at y - D(y), positions clamped to the image (the workload's literal wording)."""
     rng = np.random.default_rng(seed)
     tex = Sinusoids(rng)
     x, y = _grid(H, W)
@@ -108,9 +112,29 @@ def sinusoid_pair(H=48, W=64, seed=0, sigma=0.01, left=(1.5, -0.5), right=(-0.75
     ut = np.where(half, left[0], right[0])
     vt = np.where(half, left[1], right[1])
     f0 = tex(x, y)
+    if render == "bilinear":
+        lo, hi = float(f0.min()), float(f0.max())
+        g0 = (f0 - lo) * (1.0 / (hi - lo) if hi > lo else 1.0) + rng.normal(0.0, sigma, size=f0.shape)
+        I0 = np.clip(g0, 0.0, 1.0).astype(np.float32)
+        I1 = _bilinear(I0.astype(np.float64), x - ut, y - vt).astype(np.float32)
+        return Pair(I0, I1, ut.astype(np.float32), vt.astype(np.float32))
+    if render != "analytic":
+        raise ValueError("render must be 'analytic' or 'bilinear'")
     f1 = tex(x - ut, y - vt)    # frame 1 at y shows the frame-0 point y - D(y)
     I0, I1 = _finish(rng, f0, f1, sigma)
     return Pair(I0, I1, ut.astype(np.float32), vt.astype(np.float32))
+
+
+def _bilinear(img, xs, ys):
+    """Bilinear samples of img at (xs, ys), positions clamped to [0, W-1] x [0, H-1]."""
+    H, W = img.shape
+    xs, ys = np.clip(xs, 0.0, W - 1.0), np.clip(ys, 0.0, H - 1.0)
+    x0, y0 = np.floor(xs).astype(np.int64), np.floor(ys).astype(np.int64)
+    fx, fy = xs - x0, ys - y0
+    x1, y1 = np.minimum(x0 + 1, W - 1), np.minimum(y0 + 1, H - 1)
+    top = (1.0 - fx) * img[y0, x0] + fx * img[y0, x1]
+    bot = (1.0 - fx) * img[y1, x0] + fx * img[y1, x1]
+    return (1.0 - fy) * top + fy * bot
 
 
 def _affine(W, H, rot_deg, zoom, tx, ty):

@@ -252,6 +252,18 @@ def test_schedule_64x48_strong_data_term(ctx, orc, name):
     assert np.hypot(u - pr.u_true, v - pr.v_true).mean() < 0.1
 
 
+@pytest.mark.parametrize("lam", [0.05, 5.0])
+@pytest.mark.parametrize("name", list(METHODS))
+def test_schedule_64x48_bilinear_warped_pair(ctx, orc, name, lam):
+    """The 64 x 48 workload in its literal form: frame 1 is frame 0 (noise included) resampled
+    bilinearly by the piecewise-constant motion; 3 levels, 5 warps, 50 iterations."""
+    pr = synth.sinusoid_pair(render="bilinear")
+    u, v, ru, rv, st, rst = _solve_pair(ctx, orc, pr, 3, 5, 50, lam, METHODS[name])
+    mu, mv, epe = _flow_errors(u, v, ru, rv)
+    assert mu <= 1e-3 and mv <= 1e-3 and epe <= 1e-2, (mu, mv, epe)
+    assert st["iters_run"] == rst["iters_run"]
+
+
 def test_plain_engine_matches_fused(ctx, orc):
     pr = synth.sinusoid_pair()
     out = []

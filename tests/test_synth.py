@@ -72,6 +72,21 @@ def test_batch_sizes_and_motion(n):
         assert d.max() <= 15.0 + 0.05 * np.hypot(W / 2.0, H / 2.0) + 1e-6
 
 
+def test_sinusoid_pair_bilinear_rendering():
+    from scipy import ndimage
+    a = synth.sinusoid_pair()
+    assert np.array_equal(a.I1, synth.sinusoid_pair(render="analytic").I1)
+    p = synth.sinusoid_pair(render="bilinear")
+    H, W = p.I0.shape
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    ys, xs = np.clip(y - p.v_true, 0, H - 1), np.clip(x - p.u_true, 0, W - 1)
+    ref = ndimage.map_coordinates(p.I0.astype(np.float64), [ys, xs], order=1, mode="nearest")
+    assert np.max(np.abs(p.I1 - ref)) <= 6e-8
+    assert np.array_equal(p.u_true, a.u_true) and np.array_equal(p.v_true, a.v_true)
+    with pytest.raises(ValueError):
+        synth.sinusoid_pair(render="nearest")
+
+
 def test_batch_pairs_in_workers_equal_serial_and_extend_shorter_batches():
     serial = synth.batch_pairs(n=6)
     pooled = synth.batch_pairs(n=6, workers=2)
