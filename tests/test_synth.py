@@ -97,6 +97,19 @@ def test_batch_pairs_in_workers_equal_serial_and_extend_shorter_batches():
             assert np.array_equal(getattr(a, k), getattr(b, k))
 
 
+def test_batch_pairs_fall_back_to_threads_without_a_process_pool(monkeypatch):
+    import concurrent.futures as cf
+
+    class NoPool:
+        def __init__(self, *a, **k):
+            raise OSError("no POSIX semaphores here")
+
+    monkeypatch.setattr(cf, "ProcessPoolExecutor", NoPool)
+    got = synth.batch_pairs(n=3, workers=2)
+    for a, b in zip(synth.batch_pairs(n=3), got):
+        assert np.array_equal(a.I0, b.I0) and np.array_equal(a.I1, b.I1)
+
+
 def test_serving_mix_and_arrivals():
     sizes = synth.serve_sizes(2000)
     frac = {s: sizes.count(s) / len(sizes) for s, _ in synth.SERVE_MIX}
