@@ -272,7 +272,9 @@ of_status of_upsample(const float *coarse, int Hc, int Wc, int pc, float *fine, 
 of_status of_derivatives(const float *I, int H, int W, int pitch, float *Ix, float *Iy, void *stream);
 
 /* Warping and linearisation around d0 = (u0, v0): Ix, Iy = I1x, I1y sampled bilinearly at
- * (x + u0, y + v0) clamped to the image, It = I1(x + d0) - I0 - Ix u0 - Iy v0.  ms_max: device
+ * (x + u0, y + v0) clamped to the image, It = I1(x + d0) - I0 - Ix u0 - Iy v0, computed in FP64
+ * and rounded once to the stored type (Sec. 1: rho(d) = grad I^T d + I_t; reading: its
+ * linearisation around d0 inside Sec. 4's coarse-to-fine warping, bilinear sampling).  ms_max: device
  * pointer to one float that receives max(beta^2 + Ix^2 + Iy^2) (it must hold 0 or a smaller
  * non-negative value on entry; the kernel raises it). */
 of_status of_warp_linearise(const float *I0, const float *I1, const float *I1x, const float *I1y,
